@@ -1,0 +1,208 @@
+/*
+ * mdhp.h -- C ABI of the GB300 (sm_103a) MDHP-GDS library.
+ *
+ * MDHP-GDS (arXiv 2411.10258, Sec. IV-B) fits the parameters of an
+ * exponential-kernel multi-dimensional Hawkes process to windows of
+ * time-stamped messages by gradient ascent on the log-likelihood:
+ *
+ *   lambda_i(t) = mu_i + sum_j sum_{k: t_k < t, u_k = j} w_k alpha_ij exp(-beta_ij (t - t_k))
+ *                                                   (Sec. II, MDHP intensity eq.; mu is the paper's theta)
+ *   lnL = sum_n ln lambda_{u_n}(t_n)                                        (Part1)
+ *         - T_span sum_i mu_i                                               (Part2)
+ *         + sum_ij (alpha_ij / beta_ij) sum_{k: u_k = j} w_k (exp(-beta_ij (T_span - t_k)) - 1)   (Part3)
+ *                                                   (Sec. IV-B.1 closed-form lnL eq.; App. B)
+ *
+ * w_k are optional per-event weights (NULL = 1, which is the paper's model).
+ * Index convention: alpha is row-major [M][M], row = target i, column = source j,
+ * as in the intensity formula.  beta has one of three shapes (mdhp_beta_mode).
+ * Events that share a timestamp do not excite one another (the sum is strict).
+ *
+ * Conventions for every entry point:
+ *   - All array pointers are DEVICE pointers unless stated otherwise, owned by
+ *     the caller; the library never frees them.  The library allocates device
+ *     memory only inside an mdhp_plan (mdhp_plan_create) and frees it in
+ *     mdhp_plan_destroy.
+ *   - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t,
+ *     NULL = the legacy default stream).
+ *   - Argument errors are returned synchronously and nothing is launched.
+ *     Data errors are reported per window in win_status[] (int32 mdhp_status);
+ *     the call itself then still returns MDHP_OK.  MDHP_E_CUDA means a launch
+ *     failed; mdhp_last_error() gives the text.
+ *   - Gradients are of lnL itself (ascent direction), not of -lnL.
+ *   - Matrix-shaped beta (MDHP_BETA_MATRIX) is not supported on the GPU path:
+ *     such calls return MDHP_E_UNSUPPORTED.
+ *   - M (number of event types / message IDs) is limited to 1..64.
+ */
+#ifndef MDHP_H_
+#define MDHP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MDHP_OK = 0,
+  MDHP_E_ARG = 1,          /* bad argument (sizes, NULL, unsupported M) */
+  MDHP_E_UNSORTED = 2,     /* window timestamps not non-decreasing */
+  MDHP_E_ID_RANGE = 3,     /* an id outside [0, M) */
+  MDHP_E_TIME_RANGE = 4,   /* a timestamp outside [0, T_span], or T_span < 0 / not finite */
+  MDHP_E_NONFINITE = 5,    /* NaN/Inf in inputs, or lnL / gradient not finite */
+  MDHP_E_MAXITER = 6,      /* fit: tolerance requested but not met within max_iters */
+  MDHP_E_TIMEOUT = 7,      /* reserved: a bounded device-side wait gave up */
+  MDHP_E_CUDA = 8,         /* a CUDA call failed */
+  MDHP_E_NOMEM = 9,        /* plan allocation failed */
+  MDHP_E_UNSUPPORTED = 10  /* valid request this build does not implement */
+} mdhp_status;
+
+typedef enum {
+  MDHP_BETA_SCALAR = 0,     /* beta[B]: one decay per window */
+  MDHP_BETA_PER_SOURCE = 1, /* beta[B][M]: beta_ij = beta_j (decay of source j's excitation) */
+  MDHP_BETA_MATRIX = 2      /* beta[B][M][M]: the paper's general (D, D) form (oracle only) */
+} mdhp_beta_mode;
+
+/*
+ * A batch of B independent windows in CSR layout (replaces the paper's
+ * padding to maxTimeLen, Sec. IV-B.3 Stage 1).
+ *   offsets   int64[B+1], offsets[0] = 0, non-decreasing; window b holds events
+ *             offsets[b] .. offsets[b+1]-1.
+ *   t         float32[n_events], seconds from the window start, non-decreasing
+ *             within a window, 0 <= t <= T_span[b].
+ *   id        int16[n_events], event type (message ID) in [0, M).
+ *   T_span    float32[B], observation length of each window (the integral of
+ *             the compensator runs over [0, T_span]).
+ *   weights   float32[n_events] or NULL.
+ *   max_events  an upper bound on events per window, 0 = unknown.  When it is
+ *             known and small enough, windows are staged in shared memory;
+ *             a window longer than a stated max_events gets MDHP_E_ARG.
+ */
+typedef struct {
+  int32_t B;
+  int32_t M;
+  int64_t n_events;
+  const int64_t *offsets;
+  const float *t;
+  const int16_t *id;
+  const float *T_span;
+  const float *weights;
+  int32_t beta_mode;
+  int32_t max_events;
+} mdhp_batch;
+
+/*
+ * lnL and its gradient for every window at the given parameters
+ * (closed-form lnL, Sec. IV-B.1; gradient by the same O(N M) recursion).
+ *   mu     float32[B][M]           (the paper's theta)
+ *   alpha  float32[B][M][M]        row = target
+ *   beta   float32[B] | [B][M]     per batch->beta_mode
+ * Outputs (device):
+ *   loglik    float64[B]             lnL per window (NaN if the window is invalid)
+ *   g_mu      float32[B][M]          d lnL / d mu
+ *   g_alpha   float32[B][M][M]       d lnL / d alpha
+ *   g_beta    float32[B] | [B][M], or NULL (skips the beta-derivative states)
+ *   g_weights float32[n_events], or NULL: d lnL / d w_k for every event
+ *   r_work    float32[n_events] caller-provided scratch, required iff
+ *             g_weights != NULL (holds 1/lambda at each event between the
+ *             forward and the reverse pass)
+ *   win_status int32[B] (mdhp_status per window)
+ */
+mdhp_status mdhp_loglik_grad(const mdhp_batch *batch, const float *mu, const float *alpha,
+                             const float *beta, double *loglik, float *g_mu, float *g_alpha,
+                             float *g_beta, float *g_weights, float *r_work, int32_t *win_status,
+                             void *stream);
+
+/*
+ * Options of the fit.  The paper fixes none of the optimiser, step, start
+ * point or stopping rule (Sec. IV-B.2: "a PyTorch optimizer"); these are the
+ * library's readings:
+ *   objective  f = lnL / max(N_w, 1) per window (scale-free step size)
+ *   optimizer  0: projected gradient ascent  theta <- max(theta + lr * grad f, floor)
+ *              1: projected Adam (adam_b1, adam_b2, adam_eps) on grad f
+ *   iteration  k = 0, 1, ...: evaluate lnL_k and its gradient at theta_k; stop when
+ *              |lnL_k - lnL_{k-1}| <= tol |lnL_k| held `patience` times in a row
+ *              (tol > 0), or k = max_iters - 1, or the evaluation is not finite
+ *              (then the previous point is restored); otherwise update.
+ *              The returned parameters are the last evaluated point.
+ *   floors     mu >= mu_floor, alpha >= alpha_floor, beta >= beta_floor
+ *   fit_beta   1: beta is updated too (per-source or scalar)
+ *   init       0: start from the parameters passed in (warm start / resume)
+ *              1: cold start, mu_i = 0.5 max(N_i,1) / T_span, alpha_ij = 0.5 beta_ij / M
+ *                 (spectral radius of alpha/beta = 0.5); beta as passed in
+ *              2: learned initializer (the plan must hold a model, see
+ *                 mdhp_plan_set_init_model); beta as passed in
+ */
+typedef struct {
+  int32_t optimizer;
+  int32_t max_iters;
+  int32_t fit_beta;
+  int32_t patience;
+  float lr;
+  float mu_floor;
+  float alpha_floor;
+  float beta_floor;
+  float adam_b1;
+  float adam_b2;
+  float adam_eps;
+  int32_t init;
+  double tol;
+} mdhp_fit_opts;
+
+/* Fills the defaults: optimizer 0, max_iters 200, fit_beta 0, patience 3,
+ * lr 1e-2, floors 1e-10 / 0 / 1e-6, Adam 0.9 / 0.999 / 1e-8, init 1, tol 0. */
+void mdhp_fit_opts_default(mdhp_fit_opts *opts);
+
+/*
+ * A plan owns the device scratch of batched fitting (length-sorted work queue,
+ * counters, sort workspace) and the tuned launch shape.  It is created for one
+ * (M, beta_mode) and at most max_windows windows of at most
+ * max_events_per_window events (0 = no stated bound: long windows are then
+ * streamed from device memory).  autotune_cache: path of a JSON file written
+ * by mdhp_plan_autotune and read here, or NULL.
+ * Not thread-safe: one plan per concurrent stream.
+ */
+typedef struct mdhp_plan mdhp_plan;
+
+mdhp_status mdhp_plan_create(mdhp_plan **plan, int32_t M, int32_t beta_mode, int32_t max_windows,
+                             int64_t max_events_per_window, const char *autotune_cache);
+void mdhp_plan_destroy(mdhp_plan *plan);
+
+/*
+ * Batched MDHP-GDS: fits every window of `batch` (B <= the plan's max_windows)
+ * in one persistent launch per length class, windows taken longest first.
+ *   mu, alpha, beta  in/out, shapes as in mdhp_loglik_grad
+ *   loglik   float64[B] lnL at the returned parameters
+ *   iters    int32[B]   number of lnL/gradient evaluations
+ *   win_status int32[B] MDHP_OK, MDHP_E_MAXITER, MDHP_E_NONFINITE or an input error
+ * Capturable in a CUDA graph (no host synchronisation, no allocation).
+ */
+mdhp_status mdhp_fit_batch(mdhp_plan *plan, const mdhp_batch *batch, const mdhp_fit_opts *opts,
+                           float *mu, float *alpha, float *beta, double *loglik, int32_t *iters,
+                           int32_t *win_status, void *stream);
+
+/* Device time (ms) of the fit kernels of the last mdhp_fit_batch call on this
+ * plan, measured with CUDA events recorded on the call's stream around them
+ * (the call synchronises on those events).  Requires timing to have been
+ * enabled with mdhp_plan_set_timing(plan, 1) before the call.  Returns <0 if
+ * no timing is available. */
+mdhp_status mdhp_plan_set_timing(mdhp_plan *plan, int32_t enable);
+float mdhp_plan_last_fit_ms(mdhp_plan *plan);
+
+/* Launch shape chosen for a length class (for tests and reports):
+ * threads per window, threads per chunk, and the shared-memory cutoff. */
+mdhp_status mdhp_plan_get_shape(const mdhp_plan *plan, int32_t *threads_per_window,
+                                int32_t *threads_per_chunk, int32_t *smem_cutoff_events);
+mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
+                                int32_t threads_per_chunk, int32_t smem_cutoff_events);
+
+/* Text of the last error in this thread (static storage). */
+const char *mdhp_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t mdhp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDHP_H_ */

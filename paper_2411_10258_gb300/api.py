@@ -1,0 +1,218 @@
+"""Python surface of the MDHP-GDS library: torch tensors in, C ABI calls out.
+
+Every computation runs in the CUDA library (``libmdhp.so``); this module only
+moves pointers, shapes and the current CUDA stream across the boundary.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _ptr(x):
+    return None if x is None else ctypes.c_void_p(x.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def nbeta(beta_mode: int, M: int) -> int:
+    return 1 if beta_mode == 0 else M
+
+
+@dataclass
+class DeviceBatch:
+    """CSR windows resident on the GPU (see include/mdhp.h, mdhp_batch)."""
+
+    M: int
+    beta_mode: int
+    offsets: torch.Tensor  # int64 [B+1]
+    t: torch.Tensor  # float32 [n]
+    id: torch.Tensor  # int16 [n]
+    T: torch.Tensor  # float32 [B]
+    weights: torch.Tensor | None = None  # float32 [n]
+    max_events: int = 0
+
+    @property
+    def B(self) -> int:
+        return int(self.T.shape[0])
+
+    @property
+    def n_events(self) -> int:
+        return int(self.t.shape[0])
+
+    def c_struct(self, weights: torch.Tensor | None = None) -> _lib.MdhpBatch:
+        w = self.weights if weights is None else weights
+        return _lib.MdhpBatch(self.B, self.M, self.n_events, _ptr(self.offsets), _ptr(self.t),
+                              _ptr(self.id), _ptr(self.T), _ptr(w), self.beta_mode,
+                              int(self.max_events))
+
+    @staticmethod
+    def from_host(batch, device="cuda", max_events: int | None = None, non_blocking=False):
+        """Copy a host batch (workload.Batch or anything with the same fields)."""
+        dev = torch.device(device)
+
+        def up(a):
+            return torch.from_numpy(np.ascontiguousarray(a)).to(dev, non_blocking=non_blocking)
+
+        cnt = np.diff(batch.offsets)
+        me = int(cnt.max()) if (max_events is None and len(cnt)) else int(max_events or 0)
+        return DeviceBatch(batch.M, batch.beta_mode, up(batch.offsets), up(batch.t), up(batch.id),
+                           up(batch.T), None if batch.weights is None else up(batch.weights), me)
+
+
+def loglik_grad(db: DeviceBatch, mu: torch.Tensor, alpha: torch.Tensor, beta: torch.Tensor,
+                beta_grad: bool = False, weight_grad: bool = False,
+                weights: torch.Tensor | None = None, stream=None) -> dict:
+    """lnL and its gradient per window (mdhp_loglik_grad).  Returns tensors
+    loglik [B] f64, g_mu [B,M], g_alpha [B,M,M], g_beta or None, g_w or None,
+    status [B] int32."""
+    lib = _lib.load()
+    B, M = db.B, db.M
+    dev = db.t.device
+    f32 = dict(dtype=torch.float32, device=dev)
+    mu = mu.contiguous().float(); alpha = alpha.contiguous().float(); beta = beta.contiguous().float()
+    out = dict(loglik=torch.empty(B, dtype=torch.float64, device=dev),
+               g_mu=torch.empty(B, M, **f32), g_alpha=torch.empty(B, M, M, **f32),
+               g_beta=torch.empty(B, nbeta(db.beta_mode, M), **f32) if beta_grad else None,
+               g_w=torch.empty(db.n_events, **f32) if weight_grad else None,
+               status=torch.empty(B, dtype=torch.int32, device=dev))
+    r_work = torch.empty(db.n_events, **f32) if weight_grad else None
+    st = db.c_struct(weights)
+    rc = lib.mdhp_loglik_grad(ctypes.byref(st), _ptr(mu), _ptr(alpha), _ptr(beta),
+                              _ptr(out["loglik"]), _ptr(out["g_mu"]), _ptr(out["g_alpha"]),
+                              _ptr(out["g_beta"]), _ptr(out["g_w"]), _ptr(r_work),
+                              _ptr(out["status"]), _stream(stream))
+    _lib.check(rc, "mdhp_loglik_grad")
+    out["_keep"] = (r_work, mu, alpha, beta)
+    return out
+
+
+@dataclass
+class FitOptions:
+    """Mirror of mdhp_fit_opts (defaults as mdhp_fit_opts_default)."""
+
+    optimizer: int = 0
+    max_iters: int = 200
+    fit_beta: int = 0
+    patience: int = 3
+    lr: float = 1e-2
+    mu_floor: float = 1e-10
+    alpha_floor: float = 0.0
+    beta_floor: float = 1e-6
+    adam_b1: float = 0.9
+    adam_b2: float = 0.999
+    adam_eps: float = 1e-8
+    init: int = 1
+    tol: float = 0.0
+
+    def c_struct(self) -> _lib.MdhpFitOpts:
+        return _lib.MdhpFitOpts(self.optimizer, self.max_iters, self.fit_beta, self.patience,
+                                self.lr, self.mu_floor, self.alpha_floor, self.beta_floor,
+                                self.adam_b1, self.adam_b2, self.adam_eps, self.init, self.tol)
+
+
+class Plan:
+    """Owns the device scratch of batched fitting (mdhp_plan)."""
+
+    def __init__(self, M: int, beta_mode: int, max_windows: int, max_events: int = 0,
+                 autotune_cache: str | None = None):
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        rc = self.lib.mdhp_plan_create(ctypes.byref(h), M, beta_mode, max_windows, max_events,
+                                       None if autotune_cache is None else autotune_cache.encode())
+        _lib.check(rc, "mdhp_plan_create")
+        self.h = h
+        self.M, self.beta_mode, self.max_windows = M, beta_mode, max_windows
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mdhp_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_timing(self, on: bool):
+        _lib.check(self.lib.mdhp_plan_set_timing(self.h, 1 if on else 0), "mdhp_plan_set_timing")
+
+    def last_fit_ms(self) -> float:
+        return float(self.lib.mdhp_plan_last_fit_ms(self.h))
+
+    def shape(self):
+        v = [ctypes.c_int32() for _ in range(3)]
+        _lib.check(self.lib.mdhp_plan_get_shape(self.h, *[ctypes.byref(x) for x in v]), "get_shape")
+        return tuple(x.value for x in v)
+
+    def set_shape(self, threads_per_window: int, threads_per_chunk: int, cutoff: int):
+        _lib.check(self.lib.mdhp_plan_set_shape(self.h, threads_per_window, threads_per_chunk, cutoff),
+                   "mdhp_plan_set_shape")
+
+    def fit(self, db: DeviceBatch, opts: FitOptions, mu: torch.Tensor, alpha: torch.Tensor,
+            beta: torch.Tensor, out: dict | None = None, stream=None) -> dict:
+        """mdhp_fit_batch; mu/alpha/beta are updated in place (float32, contiguous)."""
+        B = db.B
+        dev = db.t.device
+        if out is None:
+            out = dict(loglik=torch.empty(B, dtype=torch.float64, device=dev),
+                       iters=torch.empty(B, dtype=torch.int32, device=dev),
+                       status=torch.empty(B, dtype=torch.int32, device=dev))
+        for x in (mu, alpha, beta):
+            assert x.is_contiguous() and x.dtype == torch.float32 and x.device == dev
+        st = db.c_struct()
+        o = opts.c_struct()
+        rc = self.lib.mdhp_fit_batch(self.h, ctypes.byref(st), ctypes.byref(o), _ptr(mu),
+                                     _ptr(alpha), _ptr(beta), _ptr(out["loglik"]),
+                                     _ptr(out["iters"]), _ptr(out["status"]), _stream(stream))
+        _lib.check(rc, "mdhp_fit_batch")
+        out.update(mu=mu, alpha=alpha, beta=beta)
+        return out
+
+
+class LoglikGrad(torch.autograd.Function):
+    """lnL per window as a differentiable function of (mu, alpha, beta, weights).
+
+    forward returns lnL [B] (float64); the gradients are computed by the
+    library in the same call (one recursion pass, plus the reverse-time pass
+    for event weights), and backward scales them by grad_output per window.
+    As a loss use -LoglikGrad.apply(...).sum()."""
+
+    @staticmethod
+    def forward(ctx, db: DeviceBatch, mu, alpha, beta, weights=None):
+        need_b = ctx.needs_input_grad[3]
+        need_w = weights is not None and ctx.needs_input_grad[4]
+        out = loglik_grad(db, mu.detach(), alpha.detach(), beta.detach(), beta_grad=need_b,
+                          weight_grad=need_w, weights=None if weights is None else weights.detach())
+        bad = out["status"] != 0
+        ctx.save_for_backward(out["g_mu"], out["g_alpha"],
+                              out["g_beta"] if need_b else torch.empty(0, device=mu.device),
+                              out["g_w"] if need_w else torch.empty(0, device=mu.device),
+                              db.offsets)
+        ctx.need_b, ctx.need_w = need_b, need_w
+        ctx.beta_shape = beta.shape
+        ll = out["loglik"]
+        ctx.mark_non_differentiable(bad)
+        return ll, bad
+
+    @staticmethod
+    def backward(ctx, g_ll, _g_bad):
+        g_mu, g_alpha, g_beta, g_w, offsets = ctx.saved_tensors
+        go = g_ll.to(torch.float32)
+        d_mu = g_mu * go[:, None]
+        d_alpha = g_alpha * go[:, None, None]
+        d_beta = (g_beta * go[:, None]).reshape(ctx.beta_shape) if ctx.need_b else None
+        d_w = None
+        if ctx.need_w:
+            counts = offsets[1:] - offsets[:-1]
+            d_w = g_w * torch.repeat_interleave(go, counts)
+        return None, d_mu, d_alpha, d_beta, d_w

@@ -1,0 +1,20 @@
+// Kernel instantiations for template capacity M = 32.
+#include "k_inst.cuh"
+
+namespace mdhp {
+
+LlgFn get_llg_m32(int SPL, int BM, bool learn, bool stage) {
+  MDHP_LLG_CASE(32, 2)
+  MDHP_LLG_CASE(32, 4)
+  return nullptr;
+}
+
+FitFn get_fit_m32(int SPL, int BM, bool learn, bool stage) {
+  MDHP_FIT_CASE(32, 2)
+  MDHP_FIT_CASE(32, 4)
+  return nullptr;
+}
+
+WgFn get_wg_m32(int BM) { return BM == 0 ? k_weight_grad<32, 0> : k_weight_grad<32, 1>; }
+
+}  // namespace mdhp

@@ -1,0 +1,18 @@
+// Kernel instantiations for template capacity M = 8.
+#include "k_inst.cuh"
+
+namespace mdhp {
+
+LlgFn get_llg_m8(int SPL, int BM, bool learn, bool stage) {
+  MDHP_LLG_CASE(8, 1)
+  return nullptr;
+}
+
+FitFn get_fit_m8(int SPL, int BM, bool learn, bool stage) {
+  MDHP_FIT_CASE(8, 1)
+  return nullptr;
+}
+
+WgFn get_wg_m8(int BM) { return BM == 0 ? k_weight_grad<8, 0> : k_weight_grad<8, 1>; }
+
+}  // namespace mdhp

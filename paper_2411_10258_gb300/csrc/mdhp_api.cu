@@ -1,0 +1,436 @@
+// C ABI of the MDHP-GDS library (declared in include/mdhp.h).
+#include <cub/device/device_radix_sort.cuh>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "mdhp.h"
+#include "mdhp_dispatch.h"
+
+namespace mdhp {
+
+static thread_local std::string g_last_error;
+
+static mdhp_status fail(mdhp_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+static mdhp_status cuda_check(const char *what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MDHP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return MDHP_OK;
+}
+
+// Template capacity for a runtime M.
+static int cap_of(int M) {
+  if (M <= 4) return 4;
+  if (M <= 8) return 8;
+  if (M <= 16) return 16;
+  if (M <= 32) return 32;
+  return 64;
+}
+
+LlgFn get_llg(int M, int SPL, int BM, bool learn, bool stage) {
+  switch (M) {
+    case 4: return get_llg_m4(SPL, BM, learn, stage);
+    case 8: return get_llg_m8(SPL, BM, learn, stage);
+    case 16: return get_llg_m16(SPL, BM, learn, stage);
+    case 32: return get_llg_m32(SPL, BM, learn, stage);
+    case 64: return get_llg_m64(SPL, BM, learn, stage);
+  }
+  return nullptr;
+}
+FitFn get_fit(int M, int SPL, int BM, bool learn, bool stage) {
+  switch (M) {
+    case 4: return get_fit_m4(SPL, BM, learn, stage);
+    case 8: return get_fit_m8(SPL, BM, learn, stage);
+    case 16: return get_fit_m16(SPL, BM, learn, stage);
+    case 32: return get_fit_m32(SPL, BM, learn, stage);
+    case 64: return get_fit_m64(SPL, BM, learn, stage);
+  }
+  return nullptr;
+}
+WgFn get_wg(int M, int BM) {
+  switch (M) {
+    case 4: return get_wg_m4(BM);
+    case 8: return get_wg_m8(BM);
+    case 16: return get_wg_m16(BM);
+    case 32: return get_wg_m32(BM);
+    case 64: return get_wg_m64(BM);
+  }
+  return nullptr;
+}
+
+// Default launch shape per template capacity: threads per window and threads
+// per chunk (sources split across SPL threads), and the longest window staged
+// in shared memory.
+struct Shape {
+  int nt, spl, cutoff;
+};
+static Shape default_shape(int Mt) {
+  switch (Mt) {
+    case 4: return {128, 1, 16384};
+    case 8: return {128, 1, 12288};
+    case 16: return {128, 1, 10240};
+    case 32: return {128, 2, 10240};
+    default: return {256, 4, 8192};
+  }
+}
+
+static int max_dyn_smem() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  return v;
+}
+
+static int num_sms() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return v;
+}
+
+static mdhp_status prepare_kernel(const void *fn, int smem) {
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return fail(MDHP_E_CUDA, "cudaFuncSetAttribute(%d bytes): %s", smem,
+                  cudaGetErrorString(cudaGetLastError()));
+  }
+  return MDHP_OK;
+}
+
+static mdhp_status check_batch(const mdhp_batch *b) {
+  if (!b) return fail(MDHP_E_ARG, "batch is NULL");
+  if (b->B < 0) return fail(MDHP_E_ARG, "B < 0");
+  if (b->M < 1 || b->M > 64) return fail(MDHP_E_ARG, "M = %d outside 1..64", b->M);
+  if (b->beta_mode == MDHP_BETA_MATRIX)
+    return fail(MDHP_E_UNSUPPORTED, "matrix-shaped beta is not implemented on the GPU path");
+  if (b->beta_mode != MDHP_BETA_SCALAR && b->beta_mode != MDHP_BETA_PER_SOURCE)
+    return fail(MDHP_E_ARG, "beta_mode %d", b->beta_mode);
+  if (b->n_events < 0) return fail(MDHP_E_ARG, "n_events < 0");
+  if (b->n_events > 0 && (!b->t || !b->id)) return fail(MDHP_E_ARG, "t/id NULL");
+  if (b->B > 0 && (!b->offsets || !b->T_span)) return fail(MDHP_E_ARG, "offsets/T_span NULL");
+  if (b->max_events < 0) return fail(MDHP_E_ARG, "max_events < 0");
+  return MDHP_OK;
+}
+
+}  // namespace mdhp
+
+using namespace mdhp;
+
+struct mdhp_plan {
+  int M, Mt, beta_mode, max_windows;
+  int64_t max_events;
+  Shape shape;
+  int *keys = nullptr, *keys_sorted = nullptr, *idx = nullptr, *order = nullptr;
+  int *ctl = nullptr;  // [0] queue long, [1] queue short, [2..3] range long, [4..5] range short
+  void *sort_tmp = nullptr;
+  size_t sort_tmp_bytes = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  int timing = 0, timed = 0;
+};
+
+extern "C" {
+
+const char *mdhp_last_error(void) { return g_last_error.c_str(); }
+
+int32_t mdhp_version(void) { return 100; }
+
+void mdhp_fit_opts_default(mdhp_fit_opts *o) {
+  if (!o) return;
+  o->optimizer = 0;
+  o->max_iters = 200;
+  o->fit_beta = 0;
+  o->patience = 3;
+  o->lr = 1e-2f;
+  o->mu_floor = 1e-10f;
+  o->alpha_floor = 0.f;
+  o->beta_floor = 1e-6f;
+  o->adam_b1 = 0.9f;
+  o->adam_b2 = 0.999f;
+  o->adam_eps = 1e-8f;
+  o->init = 1;
+  o->tol = 0.0;
+}
+
+mdhp_status mdhp_loglik_grad(const mdhp_batch *batch, const float *mu, const float *alpha,
+                             const float *beta, double *loglik, float *g_mu, float *g_alpha,
+                             float *g_beta, float *g_weights, float *r_work, int32_t *win_status,
+                             void *stream) {
+  mdhp_status s = check_batch(batch);
+  if (s != MDHP_OK) return s;
+  const int B = batch->B, M = batch->M, BM = batch->beta_mode;
+  if (B == 0) return MDHP_OK;
+  if (!mu || !alpha || !beta || !loglik || !g_mu || !g_alpha || !win_status)
+    return fail(MDHP_E_ARG, "NULL parameter/output pointer");
+  if (g_weights && !r_work) return fail(MDHP_E_ARG, "g_weights requires r_work");
+  const int Mt = cap_of(M);
+  const Shape sh = default_shape(Mt);
+  const bool learn = g_beta != nullptr;
+  const bool stage = batch->max_events > 0 && batch->max_events <= sh.cutoff;
+  LlgFn fn = get_llg(Mt, sh.spl, BM, learn, stage);
+  if (!fn) return fail(MDHP_E_UNSUPPORTED, "no kernel for M=%d", M);
+  const int NC = sh.nt / sh.spl;
+  LlgArgs a{};
+  a.offsets = batch->offsets; a.t = batch->t; a.id = batch->id; a.T = batch->T_span;
+  a.w = batch->weights; a.mu = mu; a.alpha = alpha; a.beta = beta; a.loglik = loglik;
+  a.g_mu = g_mu; a.g_alpha = g_alpha; a.g_beta = g_beta;
+  a.r_out = g_weights ? r_work : nullptr;
+  a.status = win_status; a.B = B; a.Mrt = M; a.NC = NC;
+  a.ev_cap = stage ? batch->max_events : 0;
+  a.carve = make_carve(Mt, NC, a.ev_cap, batch->weights != nullptr, learn, false, false);
+  if (a.carve.total > max_dyn_smem())
+    return fail(MDHP_E_ARG, "shared memory %d > %d", a.carve.total, max_dyn_smem());
+  if ((s = prepare_kernel((const void *)fn, a.carve.total)) != MDHP_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  fn<<<B, sh.nt, a.carve.total, st>>>(a);
+  if ((s = cuda_check("k_loglik_grad")) != MDHP_OK) return s;
+  if (g_weights) {
+    WgFn wf = get_wg(Mt, BM);
+    WgArgs w{};
+    w.offsets = batch->offsets; w.t = batch->t; w.id = batch->id; w.T = batch->T_span;
+    w.alpha = alpha; w.beta = beta; w.r = r_work; w.g_w = g_weights; w.status = win_status;
+    w.Mrt = M;
+    const int nt = 128 > Mt ? 128 : Mt;
+    w.NC = nt;
+    const int smem = (Mt * (Mt + 1) + 3 * Mt + 2 * (nt + 1) + nt * Mt) * 4;
+    if (smem > max_dyn_smem()) return fail(MDHP_E_ARG, "weight-grad shared memory %d", smem);
+    if ((s = prepare_kernel((const void *)wf, smem)) != MDHP_OK) return s;
+    wf<<<B, nt, smem, st>>>(w);
+    if ((s = cuda_check("k_weight_grad")) != MDHP_OK) return s;
+  }
+  return MDHP_OK;
+}
+
+// --- plans -----------------------------------------------------------------
+
+__global__ void k_lengths(const int64_t *offsets, int B, int *keys, int *idx) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) {
+    const int64_t n = offsets[b + 1] - offsets[b];
+    keys[b] = n > 0x7ffffff0LL ? 0x7ffffff0 : (n < 0 ? 0 : (int)n);
+    idx[b] = b;
+  }
+}
+
+// Sorted keys (descending) -> number of windows longer than the cutoff;
+// writes the two work ranges and clears the queue counters.  Without a
+// streamed launch every window goes to the staged kernel, which reports
+// MDHP_E_ARG for a window longer than its staging capacity.
+__global__ void k_split(const int *keys_sorted, int B, int cutoff, int has_long, int *ctl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int lo = 0, hi = has_long ? B : 0;  // first position with key <= cutoff
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (keys_sorted[mid] > cutoff) lo = mid + 1;
+      else hi = mid;
+    }
+    ctl[0] = 0;
+    ctl[1] = 0;
+    ctl[2] = 0;
+    ctl[3] = lo;
+    ctl[4] = lo;
+    ctl[5] = B;
+  }
+}
+
+mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int32_t max_windows,
+                             int64_t max_events_per_window, const char *autotune_cache) {
+  (void)autotune_cache;
+  if (!out) return fail(MDHP_E_ARG, "plan out-pointer NULL");
+  *out = nullptr;
+  if (M < 1 || M > 64) return fail(MDHP_E_ARG, "M = %d outside 1..64", M);
+  if (beta_mode == MDHP_BETA_MATRIX)
+    return fail(MDHP_E_UNSUPPORTED, "matrix-shaped beta is not implemented on the GPU path");
+  if (beta_mode != 0 && beta_mode != 1) return fail(MDHP_E_ARG, "beta_mode %d", beta_mode);
+  if (max_windows < 1) return fail(MDHP_E_ARG, "max_windows < 1");
+  if (max_events_per_window < 0) return fail(MDHP_E_ARG, "max_events_per_window < 0");
+  mdhp_plan *p = new mdhp_plan();
+  p->M = M;
+  p->Mt = cap_of(M);
+  p->beta_mode = beta_mode;
+  p->max_windows = max_windows;
+  p->max_events = max_events_per_window;
+  p->shape = default_shape(p->Mt);
+  bool ok = true;
+  ok &= cudaMalloc(&p->keys, sizeof(int) * max_windows) == cudaSuccess;
+  ok &= cudaMalloc(&p->keys_sorted, sizeof(int) * max_windows) == cudaSuccess;
+  ok &= cudaMalloc(&p->idx, sizeof(int) * max_windows) == cudaSuccess;
+  ok &= cudaMalloc(&p->order, sizeof(int) * max_windows) == cudaSuccess;
+  ok &= cudaMalloc(&p->ctl, sizeof(int) * 8) == cudaSuccess;
+  if (ok) {
+    cub::DeviceRadixSort::SortPairsDescending(nullptr, p->sort_tmp_bytes, p->keys, p->keys_sorted,
+                                              p->idx, p->order, max_windows);
+    ok &= cudaMalloc(&p->sort_tmp, p->sort_tmp_bytes > 0 ? p->sort_tmp_bytes : 16) == cudaSuccess;
+  }
+  ok &= cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) == cudaSuccess;
+  ok &= cudaEventCreate(&p->ev_t0) == cudaSuccess;
+  ok &= cudaEventCreate(&p->ev_t1) == cudaSuccess;
+  if (!ok) {
+    mdhp_plan_destroy(p);
+    cudaGetLastError();
+    return fail(MDHP_E_NOMEM, "plan allocation failed");
+  }
+  *out = p;
+  return MDHP_OK;
+}
+
+void mdhp_plan_destroy(mdhp_plan *p) {
+  if (!p) return;
+  cudaFree(p->keys);
+  cudaFree(p->keys_sorted);
+  cudaFree(p->idx);
+  cudaFree(p->order);
+  cudaFree(p->ctl);
+  cudaFree(p->sort_tmp);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->ev_t0) cudaEventDestroy(p->ev_t0);
+  if (p->ev_t1) cudaEventDestroy(p->ev_t1);
+  delete p;
+}
+
+mdhp_status mdhp_plan_set_timing(mdhp_plan *p, int32_t enable) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  p->timing = enable ? 1 : 0;
+  p->timed = 0;
+  return MDHP_OK;
+}
+
+float mdhp_plan_last_fit_ms(mdhp_plan *p) {
+  if (!p || !p->timed) return -1.f;
+  if (cudaEventSynchronize(p->ev_t1) != cudaSuccess) return -1.f;
+  float ms = -1.f;
+  if (cudaEventElapsedTime(&ms, p->ev_t0, p->ev_t1) != cudaSuccess) return -1.f;
+  return ms;
+}
+
+mdhp_status mdhp_plan_get_shape(const mdhp_plan *p, int32_t *nt, int32_t *spl, int32_t *cutoff) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  if (nt) *nt = p->shape.nt;
+  if (spl) *spl = p->shape.spl;
+  if (cutoff) *cutoff = p->shape.cutoff;
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_plan_set_shape(mdhp_plan *p, int32_t nt, int32_t spl, int32_t cutoff) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  if (nt < 32 || nt > 512 || nt % 32 != 0) return fail(MDHP_E_ARG, "threads per window %d", nt);
+  if (nt < p->Mt) return fail(MDHP_E_ARG, "threads per window must be >= %d", p->Mt);
+  if (!get_fit(p->Mt, spl, p->beta_mode, false, true))
+    return fail(MDHP_E_UNSUPPORTED, "threads per chunk %d not built for M<=%d", spl, p->Mt);
+  if (cutoff < 0) return fail(MDHP_E_ARG, "cutoff < 0");
+  p->shape = Shape{nt, spl, cutoff};
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit_opts *o,
+                           float *mu, float *alpha, float *beta, double *loglik, int32_t *iters,
+                           int32_t *win_status, void *stream) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  mdhp_status s = check_batch(batch);
+  if (s != MDHP_OK) return s;
+  if (!o) return fail(MDHP_E_ARG, "opts NULL");
+  if (batch->M != p->M || batch->beta_mode != p->beta_mode)
+    return fail(MDHP_E_ARG, "batch (M=%d, beta_mode=%d) does not match plan (M=%d, %d)", batch->M,
+                batch->beta_mode, p->M, p->beta_mode);
+  if (batch->B > p->max_windows) return fail(MDHP_E_ARG, "B=%d > plan max_windows=%d", batch->B, p->max_windows);
+  if (o->max_iters < 1) return fail(MDHP_E_ARG, "max_iters < 1");
+  if (o->optimizer != 0 && o->optimizer != 1) return fail(MDHP_E_ARG, "optimizer %d", o->optimizer);
+  if (o->init < 0 || o->init > 2) return fail(MDHP_E_ARG, "init %d", o->init);
+  if (o->init == 2) return fail(MDHP_E_UNSUPPORTED, "learned initializer not loaded in this plan");
+  if (o->patience < 1) return fail(MDHP_E_ARG, "patience < 1");
+  if (!mu || !alpha || !beta || !loglik || !iters || !win_status)
+    return fail(MDHP_E_ARG, "NULL parameter/output pointer");
+  const int B = batch->B;
+  if (B == 0) return MDHP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Shape sh = p->shape;
+  const int NC = sh.nt / sh.spl;
+  const bool learn = o->fit_beta != 0;
+  // staging capacity: the stated bound if it fits under the cutoff, else the cutoff
+  int64_t bound = batch->max_events > 0 ? batch->max_events : p->max_events;
+  int ev_cap = (bound > 0 && bound < sh.cutoff) ? (int)bound : sh.cutoff;
+  const bool need_long = !(bound > 0 && bound <= sh.cutoff);
+
+  k_lengths<<<(B + 255) / 256, 256, 0, st>>>(batch->offsets, B, p->keys, p->idx);
+  if ((s = cuda_check("k_lengths")) != MDHP_OK) return s;
+  size_t tmp = p->sort_tmp_bytes;
+  if (cub::DeviceRadixSort::SortPairsDescending(p->sort_tmp, tmp, p->keys, p->keys_sorted, p->idx,
+                                                p->order, B, 0, 32, st) != cudaSuccess)
+    return cuda_check("radix sort");
+  k_split<<<1, 32, 0, st>>>(p->keys_sorted, B, ev_cap, need_long ? 1 : 0, p->ctl);
+  if ((s = cuda_check("k_split")) != MDHP_OK) return s;
+
+  FitArgs a{};
+  a.offsets = batch->offsets; a.t = batch->t; a.id = batch->id; a.T = batch->T_span;
+  a.w = batch->weights; a.mu = mu; a.alpha = alpha; a.beta = beta; a.loglik = loglik;
+  a.iters = iters; a.status = win_status; a.order = p->order;
+  a.Mrt = batch->M; a.NC = NC;
+  a.optimizer = o->optimizer; a.max_iters = o->max_iters; a.fit_beta = o->fit_beta;
+  a.patience = o->patience; a.init = o->init; a.lr = o->lr; a.mu_floor = o->mu_floor;
+  a.alpha_floor = o->alpha_floor; a.beta_floor = o->beta_floor; a.b1 = o->adam_b1;
+  a.b2 = o->adam_b2; a.eps = o->adam_eps; a.tol = o->tol;
+
+  if (p->timing) cudaEventRecord(p->ev_t0, st);
+  if (need_long) {
+    FitFn fl = get_fit(p->Mt, sh.spl, p->beta_mode, learn, false);
+    if (!fl) return fail(MDHP_E_UNSUPPORTED, "no streamed fit kernel for this shape");
+    FitArgs al = a;
+    al.queue = p->ctl + 0;
+    al.range = p->ctl + 2;
+    al.ev_cap = 0;
+    al.carve = make_carve(p->Mt, NC, 0, batch->weights != nullptr, learn, o->optimizer == 1, true);
+    if ((s = prepare_kernel((const void *)fl, al.carve.total)) != MDHP_OK) return s;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fl, sh.nt, al.carve.total);
+    const int grid = num_sms() * (occ > 0 ? occ : 1);
+    fl<<<grid, sh.nt, al.carve.total, st>>>(al);
+    if ((s = cuda_check("k_fit (streamed)")) != MDHP_OK) return s;
+  }
+  {
+    FitFn fs = get_fit(p->Mt, sh.spl, p->beta_mode, learn, true);
+    if (!fs) return fail(MDHP_E_UNSUPPORTED, "no staged fit kernel for this shape");
+    FitArgs as = a;
+    as.queue = p->ctl + 1;
+    as.range = p->ctl + 4;
+    as.ev_cap = ev_cap;
+    as.carve = make_carve(p->Mt, NC, ev_cap, batch->weights != nullptr, learn, o->optimizer == 1, true);
+    if (as.carve.total > max_dyn_smem())
+      return fail(MDHP_E_ARG, "shared memory %d > %d (lower the cutoff)", as.carve.total, max_dyn_smem());
+    if ((s = prepare_kernel((const void *)fs, as.carve.total)) != MDHP_OK) return s;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fs, sh.nt, as.carve.total);
+    int grid = num_sms() * (occ > 0 ? occ : 1);
+    if (grid > B) grid = B;
+    fs<<<grid, sh.nt, as.carve.total, st>>>(as);
+    if ((s = cuda_check("k_fit (staged)")) != MDHP_OK) return s;
+  }
+  if (p->timing) {
+    cudaEventRecord(p->ev_t1, st);
+    p->timed = 1;
+  }
+  return MDHP_OK;
+}
+
+}  // extern "C"

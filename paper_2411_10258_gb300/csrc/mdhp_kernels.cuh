@@ -1,0 +1,403 @@
+// Kernels of the MDHP-GDS library (sm_103a).  See mdhp_solver.cuh for the
+// recursion and the chunk decomposition.
+#pragma once
+
+#include "mdhp_solver.cuh"
+
+namespace mdhp {
+
+struct LlgArgs {
+  const int64_t *offsets;
+  const float *t;
+  const int16_t *id;
+  const float *T;
+  const float *w;
+  const float *mu, *alpha, *beta;
+  double *loglik;
+  float *g_mu, *g_alpha, *g_beta, *r_out;
+  int32_t *status;
+  int B, Mrt, NC, ev_cap;
+  Carve carve;
+};
+
+struct FitArgs {
+  const int64_t *offsets;
+  const float *t;
+  const int16_t *id;
+  const float *T;
+  const float *w;
+  float *mu, *alpha, *beta;  // in/out
+  double *loglik;
+  int32_t *iters, *status;
+  const int *order;  // window order (length-sorted), nullptr = identity
+  int *queue;        // work counter, zero at launch
+  const int *range;  // device [begin, end) of order positions, or nullptr
+  int qbegin, qend;
+  int Mrt, NC, ev_cap;
+  int optimizer, max_iters, fit_beta, patience, init;
+  float lr, mu_floor, alpha_floor, beta_floor, b1, b2, eps;
+  double tol;
+  Carve carve;
+};
+
+struct WgArgs {
+  const int64_t *offsets;
+  const float *t;
+  const int16_t *id;
+  const float *T;
+  const float *alpha, *beta;
+  const float *r;      // 1/lambda per event from the forward pass
+  float *g_w;          // out
+  const int32_t *status;
+  int Mrt, NC;
+};
+
+// Load the window's parameters into shared memory (alpha padded with zeros).
+template <int M, int BM>
+__device__ void load_params(int b, int Mrt, const float *mu, const float *alpha, const float *beta,
+                            Sm<M> &sm) {
+  constexpr int AP = M + 1;
+  const int nb = BM == 0 ? 1 : Mrt;
+  for (int p = threadIdx.x; p < M * AP; p += blockDim.x) {
+    const int i = p / AP, j = p % AP;
+    sm.alpha[p] = (i < Mrt && j < Mrt) ? alpha[(int64_t)b * Mrt * Mrt + i * Mrt + j] : 0.f;
+  }
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    sm.mu[j] = j < Mrt ? mu[(int64_t)b * Mrt + j] : 0.f;
+    const float bv = (j < nb) ? beta[(int64_t)b * nb + j] : 1.f;
+    sm.beta[j] = bv;
+    sm.bl2[j] = bv * kLog2e;
+  }
+}
+
+template <int M, int SPL, int BM, bool LEARN, bool STAGE>
+__global__ void __launch_bounds__(256) k_loglik_grad(LlgArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Sm<M> sm;
+  sm.bind(smem, a.carve);
+  constexpr int AP = M + 1;
+  const int b = blockIdx.x;
+  const int Mrt = a.Mrt;
+  const int64_t o0 = a.offsets[b];
+  const int N = (int)(a.offsets[b + 1] - o0);
+  const float T = a.T[b];
+  const float *tg = a.t + o0;
+  const int16_t *ug = a.id + o0;
+  const float *wg = a.w ? a.w + o0 : nullptr;
+  int st;
+  if (STAGE && N > a.ev_cap) {
+    st = kE_ARG;
+  } else {
+    st = stage_and_validate<M, STAGE>(tg, ug, wg, N, T, Mrt, sm);
+  }
+  const int nb = BM == 0 ? 1 : Mrt;
+  if (st != kOK) {
+    if (threadIdx.x == 0) {
+      a.status[b] = st;
+      a.loglik[b] = __longlong_as_double(0x7ff8000000000000LL);
+    }
+    for (int p = threadIdx.x; p < Mrt * Mrt; p += blockDim.x) a.g_alpha[(int64_t)b * Mrt * Mrt + p] = 0.f;
+    for (int p = threadIdx.x; p < Mrt; p += blockDim.x) a.g_mu[(int64_t)b * Mrt + p] = 0.f;
+    if (a.g_beta)
+      for (int p = threadIdx.x; p < nb; p += blockDim.x) a.g_beta[(int64_t)b * nb + p] = 0.f;
+    return;
+  }
+  load_params<M, BM>(b, Mrt, a.mu, a.alpha, a.beta, sm);
+  zero_accumulators<M>(sm);
+  __syncthreads();
+  const float *tt = STAGE ? sm.ev_t : tg;
+  const int16_t *uu = STAGE ? sm.ev_u : ug;
+  const float *ww = wg ? (STAGE ? sm.ev_w : wg) : nullptr;
+  setup_chunks(a.NC, N, T, tt, sm.bnd, sm.anc);
+  prepare_states<M, SPL, BM, LEARN>(a.NC, tt, uu, ww, T, Mrt, sm);
+  const double lnl = evaluate<M, SPL, BM, LEARN>(a.NC, tt, uu, ww, T, Mrt, sm,
+                                                 a.r_out ? a.r_out + o0 : nullptr);
+  int bad = !isfinite(lnl);
+  const int np = Mrt + Mrt * Mrt + (LEARN ? nb : 0);
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const float g = grad_of<M, BM, LEARN>(p, Mrt, T, sm);
+    bad |= !isfinite(g);
+    if (p < Mrt) {
+      a.g_mu[(int64_t)b * Mrt + p] = g;
+    } else if (p < Mrt + Mrt * Mrt) {
+      a.g_alpha[(int64_t)b * Mrt * Mrt + (p - Mrt)] = g;
+    } else if (a.g_beta) {
+      a.g_beta[(int64_t)b * nb + (p - Mrt - Mrt * Mrt)] = g;
+    }
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    a.loglik[b] = lnl;
+    a.status[b] = bad ? kE_NONFINITE : kOK;
+  }
+  (void)AP;
+}
+
+template <int M, int SPL, int BM, bool LEARN, bool STAGE>
+__global__ void __launch_bounds__(256) k_fit(FitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Sm<M> sm;
+  sm.bind(smem, a.carve);
+  constexpr int AP = M + 1;
+  const int Mrt = a.Mrt;
+  const int nb = BM == 0 ? 1 : Mrt;
+  const int np = Mrt + Mrt * Mrt + nb;
+  const int nupd = a.fit_beta ? np : Mrt + Mrt * Mrt;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) sm.ctl[1] = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int q = sm.ctl[1];
+    const int qb = a.range ? a.range[0] : a.qbegin;
+    const int qe = a.range ? a.range[1] : a.qend;
+    __syncthreads();
+    if (qb + q >= qe) break;
+    const int b = a.order ? a.order[qb + q] : qb + q;
+    const int64_t o0 = a.offsets[b];
+    const int N = (int)(a.offsets[b + 1] - o0);
+    const float T = a.T[b];
+    const float *tg = a.t + o0;
+    const int16_t *ug = a.id + o0;
+    const float *wg = a.w ? a.w + o0 : nullptr;
+    int st;
+    if (STAGE && N > a.ev_cap) {
+      st = kE_ARG;
+    } else {
+      st = stage_and_validate<M, STAGE>(tg, ug, wg, N, T, Mrt, sm);
+    }
+    if (st != kOK) {
+      if (tid == 0) {
+        a.status[b] = st;
+        a.loglik[b] = __longlong_as_double(0x7ff8000000000000LL);
+        a.iters[b] = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    // starting point
+    load_params<M, BM>(b, Mrt, a.mu, a.alpha, a.beta, sm);
+    zero_accumulators<M>(sm);
+    __syncthreads();
+    if (a.init == 1) {  // cold start: mu_i = 0.5 max(N_i,1)/T, alpha_ij = 0.5 beta_ij / M
+      for (int p = tid; p < Mrt * Mrt; p += blockDim.x) {
+        const int i = p / Mrt, j = p % Mrt;
+        sm.alpha[i * AP + j] = 0.5f * sm.beta[BM == 0 ? 0 : j] / (float)Mrt;
+      }
+      for (int i = tid; i < Mrt; i += blockDim.x)
+        sm.mu[i] = 0.5f * (float)max(sm.cnt[i], 1) / T;
+    }
+    for (int p = tid; p < np; p += blockDim.x) {
+      if (a.optimizer == 1) {
+        sm.am[p] = 0.f;
+        sm.av[p] = 0.f;
+      }
+    }
+    __syncthreads();
+    const float *tt = STAGE ? sm.ev_t : tg;
+    const int16_t *uu = STAGE ? sm.ev_u : ug;
+    const float *ww = wg ? (STAGE ? sm.ev_w : wg) : nullptr;
+    setup_chunks(a.NC, N, T, tt, sm.bnd, sm.anc);
+    if (!LEARN) prepare_states<M, SPL, BM, false>(a.NC, tt, uu, ww, T, Mrt, sm);
+    const float invN = 1.f / (float)max(N, 1);
+    double lnl_prev = 0.0, lnl_out = 0.0;
+    int streak = 0, k = 0;
+    int wst = a.tol > 0.0 ? kE_MAXITER : kOK;
+    float b1t = 1.f, b2t = 1.f;
+    for (k = 0; k < a.max_iters; ++k) {
+      if (LEARN) prepare_states<M, SPL, BM, LEARN>(a.NC, tt, uu, ww, T, Mrt, sm);
+      const double val = evaluate<M, SPL, BM, LEARN>(a.NC, tt, uu, ww, T, Mrt, sm, nullptr);
+      int bad = !isfinite(val);
+      for (int p = tid; p < np; p += blockDim.x) {
+        const float g = grad_of<M, BM, LEARN>(p, Mrt, T, sm);
+        bad |= !isfinite(g);
+        sm.gbuf[p] = g;
+      }
+      bad = __syncthreads_or(bad);
+      if (bad) {
+        if (k > 0) {
+          for (int p = tid; p < nupd; p += blockDim.x) param_ref<M>(p, Mrt, sm) = sm.prev[p];
+        } else {
+          lnl_out = val;
+        }
+        wst = kE_NONFINITE;
+        __syncthreads();
+        break;
+      }
+      if (k > 0 && a.tol > 0.0 && fabs(val - lnl_prev) <= a.tol * fabs(val)) ++streak;
+      else streak = 0;
+      lnl_prev = val;
+      lnl_out = val;
+      if (a.tol > 0.0 && streak >= a.patience) { wst = kOK; ++k; break; }
+      if (k == a.max_iters - 1) { ++k; break; }
+      b1t *= a.b1;
+      b2t *= a.b2;
+      for (int p = tid; p < nupd; p += blockDim.x) {
+        const float g = sm.gbuf[p] * invN;
+        float &th = param_ref<M>(p, Mrt, sm);
+        float step;
+        if (a.optimizer == 1) {
+          const float m1 = a.b1 * sm.am[p] + (1.f - a.b1) * g;
+          const float m2 = a.b2 * sm.av[p] + (1.f - a.b2) * g * g;
+          sm.am[p] = m1;
+          sm.av[p] = m2;
+          const float mh = m1 / (1.f - b1t), vh = m2 / (1.f - b2t);
+          step = a.lr * mh / (sqrtf(vh) + a.eps);
+        } else {
+          step = a.lr * g;
+        }
+        const float fl = p < Mrt ? a.mu_floor : (p < Mrt + Mrt * Mrt ? a.alpha_floor : a.beta_floor);
+        sm.prev[p] = th;
+        th = fmaxf(th + step, fl);
+      }
+      __syncthreads();
+      zero_accumulators<M>(sm);
+      if (LEARN) {
+        for (int j = tid; j < M; j += blockDim.x) sm.bl2[j] = sm.beta[j] * kLog2e;
+      }
+      __syncthreads();
+    }
+    // write back the last evaluated point
+    for (int p = tid; p < Mrt * Mrt; p += blockDim.x)
+      a.alpha[(int64_t)b * Mrt * Mrt + p] = sm.alpha[(p / Mrt) * AP + (p % Mrt)];
+    for (int i = tid; i < Mrt; i += blockDim.x) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];
+    for (int j = tid; j < nb; j += blockDim.x) a.beta[(int64_t)b * nb + j] = sm.beta[j];
+    if (tid == 0) {
+      a.loglik[b] = lnl_out;
+      a.iters[b] = k;
+      a.status[b] = wst;
+    }
+    __syncthreads();
+  }
+}
+
+// d lnL / d w_k by the reverse-time recursion P_j(t) = sum_{n: t_n > t}
+// r_n alpha_{u_n j} exp(-beta_j (t_n - t)):  g_k = P_{u_k}(t_k) -
+// (sum_i alpha_{i u_k}) (1 - exp(-beta_{u_k} (T - t_k))) / beta_{u_k}.
+// One thread per chunk (all M sources in registers), same chunking and tie
+// rule as the forward pass, reverse scan over chunks.
+template <int M, int BM>
+__global__ void __launch_bounds__(256) k_weight_grad(WgArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int AP = M + 1;
+  const int b = blockIdx.x;
+  if (a.status && a.status[b] != kOK) return;
+  const int NC = a.NC, Mrt = a.Mrt, tid = threadIdx.x;
+  float *alpha = (float *)smem;
+  float *bl2 = alpha + M * AP;
+  float *betas = bl2 + M;
+  float *col = betas + M;
+  float *anc = col + M;
+  int *bnd = (int *)(anc + NC + 1);
+  float *enc = (float *)(bnd + NC + 1);
+  const int64_t o0 = a.offsets[b];
+  const int N = (int)(a.offsets[b + 1] - o0);
+  const float T = a.T[b];
+  const float *t = a.t + o0;
+  const int16_t *u = a.id + o0;
+  const float *r = a.r + o0;
+  const int nb = BM == 0 ? 1 : Mrt;
+  for (int p = tid; p < M * AP; p += blockDim.x) {
+    const int i = p / AP, j = p % AP;
+    alpha[p] = (i < Mrt && j < Mrt) ? a.alpha[(int64_t)b * Mrt * Mrt + i * Mrt + j] : 0.f;
+  }
+  for (int j = tid; j < M; j += blockDim.x) {
+    const float bv = j < nb ? a.beta[(int64_t)b * nb + j] : 1.f;
+    betas[j] = BM == 0 ? a.beta[b] : bv;
+    bl2[j] = betas[j] * kLog2e;
+  }
+  __syncthreads();
+  for (int j = tid; j < M; j += blockDim.x) {
+    float s = 0.f;
+    for (int i = 0; i < M; ++i) s += alpha[i * AP + j];
+    col[j] = s;
+  }
+  setup_chunks(NC, N, T, t, bnd, anc);
+  const int c = tid;
+  float P[M];
+  float b2[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) b2[j] = bl2[j];
+  // reverse pass 1: effect of chunk c at its own anchor, from a zero state at a_{c+1}
+  if (c < NC) {
+    const int b0 = bnd[c], b1 = bnd[c + 1];
+#pragma unroll
+    for (int j = 0; j < M; ++j) P[j] = 0.f;
+    float tcur = anc[c + 1];
+    int n = b1 - 1;
+    while (n >= b0) {
+      const float tgp = t[n];
+      int gs = n;
+      while (gs > b0 && t[gs - 1] == tgp) --gs;
+      const float dt = tcur - tgp;
+      if (dt > 0.f) {
+#pragma unroll
+        for (int j = 0; j < M; ++j) P[j] *= exp2f(-b2[j] * dt);
+      }
+      tcur = tgp;
+      for (int k = gs; k <= n; ++k) {
+        const float rk = r[k];
+        const float *arow = alpha + (int)u[k] * AP;
+#pragma unroll
+        for (int j = 0; j < M; ++j) P[j] = fmaf(rk, arow[j], P[j]);
+      }
+      n = gs - 1;
+    }
+    const float dt = tcur - anc[c];
+    if (dt > 0.f) {
+#pragma unroll
+      for (int j = 0; j < M; ++j) P[j] *= exp2f(-b2[j] * dt);
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j) enc[c * M + j] = P[j];
+  }
+  __syncthreads();
+  // reverse scan: enc[c] <- state at a_{c+1} carrying every later event
+  if (tid < M) {
+    const int j = tid;
+    float E = 0.f;
+    for (int cc = NC - 1; cc >= 0; --cc) {
+      const float loc = enc[cc * M + j];
+      enc[cc * M + j] = E;
+      const float D = anc[cc + 1] - anc[cc];
+      E = fmaf(exp2f(-bl2[j] * D), E, loc);
+    }
+  }
+  __syncthreads();
+  // reverse pass 2
+  if (c < NC) {
+    const int b0 = bnd[c], b1 = bnd[c + 1];
+#pragma unroll
+    for (int j = 0; j < M; ++j) P[j] = enc[c * M + j];
+    float tcur = anc[c + 1];
+    int n = b1 - 1;
+    while (n >= b0) {
+      const float tgp = t[n];
+      int gs = n;
+      while (gs > b0 && t[gs - 1] == tgp) --gs;
+      const float dt = tcur - tgp;
+      if (dt > 0.f) {
+#pragma unroll
+        for (int j = 0; j < M; ++j) P[j] *= exp2f(-b2[j] * dt);
+      }
+      tcur = tgp;
+      for (int k = gs; k <= n; ++k) {
+        const int uk = (int)u[k];
+        float pv = 0.f;
+#pragma unroll
+        for (int j = 0; j < M; ++j) pv = (j == uk) ? P[j] : pv;
+        const float bj = betas[uk];
+        const float comp = col[uk] * (-expm1f(-bj * (T - tgp))) / bj;
+        a.g_w[o0 + k] = pv - comp;
+      }
+      for (int k = gs; k <= n; ++k) {
+        const float rk = r[k];
+        const float *arow = alpha + (int)u[k] * AP;
+#pragma unroll
+        for (int j = 0; j < M; ++j) P[j] = fmaf(rk, arow[j], P[j]);
+      }
+      n = gs - 1;
+    }
+  }
+}
+
+}  // namespace mdhp
