@@ -4,14 +4,14 @@
 namespace mdhp {
 
 LlgFn get_llg_m16(int SPL, int BM, bool learn, bool stage) {
-  MDHP_LLG_CASE(16, 1)
   MDHP_LLG_CASE(16, 2)
+  MDHP_LLG_CASE(16, 4)
   return nullptr;
 }
 
 FitFn get_fit_m16(int SPL, int BM, bool learn, bool stage) {
-  MDHP_FIT_CASE(16, 1)
   MDHP_FIT_CASE(16, 2)
+  MDHP_FIT_CASE(16, 4)
   return nullptr;
 }
 

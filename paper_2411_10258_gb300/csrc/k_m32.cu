@@ -4,14 +4,14 @@
 namespace mdhp {
 
 LlgFn get_llg_m32(int SPL, int BM, bool learn, bool stage) {
-  MDHP_LLG_CASE(32, 2)
   MDHP_LLG_CASE(32, 4)
+  MDHP_LLG_CASE(32, 8)
   return nullptr;
 }
 
 FitFn get_fit_m32(int SPL, int BM, bool learn, bool stage) {
-  MDHP_FIT_CASE(32, 2)
   MDHP_FIT_CASE(32, 4)
+  MDHP_FIT_CASE(32, 8)
   return nullptr;
 }
 

@@ -4,14 +4,14 @@
 namespace mdhp {
 
 LlgFn get_llg_m64(int SPL, int BM, bool learn, bool stage) {
-  MDHP_LLG_CASE(64, 4)
   MDHP_LLG_CASE(64, 8)
+  MDHP_LLG_CASE(64, 16)
   return nullptr;
 }
 
 FitFn get_fit_m64(int SPL, int BM, bool learn, bool stage) {
-  MDHP_FIT_CASE(64, 4)
   MDHP_FIT_CASE(64, 8)
+  MDHP_FIT_CASE(64, 16)
   return nullptr;
 }
 

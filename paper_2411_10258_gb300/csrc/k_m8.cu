@@ -4,12 +4,12 @@
 namespace mdhp {
 
 LlgFn get_llg_m8(int SPL, int BM, bool learn, bool stage) {
-  MDHP_LLG_CASE(8, 1)
+  MDHP_LLG_CASE(8, 2)
   return nullptr;
 }
 
 FitFn get_fit_m8(int SPL, int BM, bool learn, bool stage) {
-  MDHP_FIT_CASE(8, 1)
+  MDHP_FIT_CASE(8, 2)
   return nullptr;
 }
 

@@ -79,12 +79,14 @@ struct Shape {
 static Shape default_shape(int Mt) {
   switch (Mt) {
     case 4: return {128, 1, 16384};
-    case 8: return {128, 1, 12288};
-    case 16: return {128, 1, 10240};
-    case 32: return {128, 2, 10240};
-    default: return {256, 4, 8192};
+    case 8: return {128, 2, 12288};
+    case 16: return {128, 4, 8192};
+    case 32: return {128, 8, 6144};
+    default: return {256, 16, 8192};
   }
 }
+
+static bool use_priv(int Mt) { return Mt <= 32; }
 
 static int max_dyn_smem() {
   static int v = -1;
@@ -195,7 +197,8 @@ mdhp_status mdhp_loglik_grad(const mdhp_batch *batch, const float *mu, const flo
   a.r_out = g_weights ? r_work : nullptr;
   a.status = win_status; a.B = B; a.Mrt = M; a.NC = NC;
   a.ev_cap = stage ? batch->max_events : 0;
-  a.carve = make_carve(Mt, NC, a.ev_cap, batch->weights != nullptr, learn, false, false);
+  a.carve = make_carve(Mt, sh.nt, sh.spl, a.ev_cap, batch->weights != nullptr, learn, false, false,
+                       use_priv(Mt));
   if (a.carve.total > max_dyn_smem())
     return fail(MDHP_E_ARG, "shared memory %d > %d", a.carve.total, max_dyn_smem());
   if ((s = prepare_kernel((const void *)fn, a.carve.total)) != MDHP_OK) return s;
@@ -400,7 +403,8 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     al.queue = p->ctl + 0;
     al.range = p->ctl + 2;
     al.ev_cap = 0;
-    al.carve = make_carve(p->Mt, NC, 0, batch->weights != nullptr, learn, o->optimizer == 1, true);
+    al.carve = make_carve(p->Mt, sh.nt, sh.spl, 0, batch->weights != nullptr, learn,
+                          o->optimizer == 1, true, use_priv(p->Mt));
     if ((s = prepare_kernel((const void *)fl, al.carve.total)) != MDHP_OK) return s;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fl, sh.nt, al.carve.total);
@@ -415,7 +419,8 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     as.queue = p->ctl + 1;
     as.range = p->ctl + 4;
     as.ev_cap = ev_cap;
-    as.carve = make_carve(p->Mt, NC, ev_cap, batch->weights != nullptr, learn, o->optimizer == 1, true);
+    as.carve = make_carve(p->Mt, sh.nt, sh.spl, ev_cap, batch->weights != nullptr, learn,
+                          o->optimizer == 1, true, use_priv(p->Mt));
     if (as.carve.total > max_dyn_smem())
       return fail(MDHP_E_ARG, "shared memory %d > %d (lower the cutoff)", as.carve.total, max_dyn_smem());
     if ((s = prepare_kernel((const void *)fs, as.carve.total)) != MDHP_OK) return s;

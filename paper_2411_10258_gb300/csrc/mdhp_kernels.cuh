@@ -2,6 +2,8 @@
 // recursion and the chunk decomposition.
 #pragma once
 
+#include <type_traits>
+
 #include "mdhp_solver.cuh"
 
 namespace mdhp {
@@ -56,11 +58,12 @@ struct WgArgs {
 template <int M, int BM>
 __device__ void load_params(int b, int Mrt, const float *mu, const float *alpha, const float *beta,
                             Sm<M> &sm) {
-  constexpr int AP = M + 1;
+  constexpr int AP = M + 4;
   const int nb = BM == 0 ? 1 : Mrt;
   for (int p = threadIdx.x; p < M * AP; p += blockDim.x) {
     const int i = p / AP, j = p % AP;
     sm.alpha[p] = (i < Mrt && j < Mrt) ? alpha[(int64_t)b * Mrt * Mrt + i * Mrt + j] : 0.f;
+    sm.oh[p] = (i == j) ? 1.f : 0.f;
   }
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
     sm.mu[j] = j < Mrt ? mu[(int64_t)b * Mrt + j] : 0.f;
@@ -71,7 +74,7 @@ __device__ void load_params(int b, int Mrt, const float *mu, const float *alpha,
 }
 
 template <int M, int SPL, int BM, bool LEARN, bool STAGE>
-__global__ void __launch_bounds__(256) k_loglik_grad(LlgArgs a) {
+__global__ void __launch_bounds__(256, 2) k_loglik_grad(LlgArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   Sm<M> sm;
   sm.bind(smem, a.carve);
@@ -103,19 +106,30 @@ __global__ void __launch_bounds__(256) k_loglik_grad(LlgArgs a) {
     return;
   }
   load_params<M, BM>(b, Mrt, a.mu, a.alpha, a.beta, sm);
-  zero_accumulators<M>(sm);
+  clear_accumulators<M, SPL>(sm);
   __syncthreads();
-  const float *tt = STAGE ? sm.ev_t : tg;
-  const int16_t *uu = STAGE ? sm.ev_u : ug;
-  const float *ww = wg ? (STAGE ? sm.ev_w : wg) : nullptr;
-  setup_chunks(a.NC, N, T, tt, sm.bnd, sm.anc);
-  prepare_states<M, SPL, BM, LEARN>(a.NC, tt, uu, ww, T, Mrt, sm);
-  const double lnl = evaluate<M, SPL, BM, LEARN>(a.NC, tt, uu, ww, T, Mrt, sm,
-                                                 a.r_out ? a.r_out + o0 : nullptr);
-  int bad = !isfinite(lnl);
+  constexpr bool FIXED = STAGE && !LEARN && BM == 0;
+  if (STAGE) {
+    const EvS ev{sm.ev_t, sm.ev_u, wg ? sm.ev_w : nullptr};
+    setup_chunks(a.NC, N, T, ev, sm.bnd, sm.anc);
+    prepare_states<M, SPL, BM, LEARN>(a.NC, ev, Mrt, sm);
+    if (FIXED) to_decays<M, SPL>(a.NC, sm);
+    evaluate<M, SPL, BM, LEARN, FIXED>(a.NC, ev, T, Mrt, sm, a.r_out ? a.r_out + o0 : nullptr);
+  } else {
+    const EvG ev{tg, ug, wg};
+    setup_chunks(a.NC, N, T, ev, sm.bnd, sm.anc);
+    prepare_states<M, SPL, BM, LEARN>(a.NC, ev, Mrt, sm);
+    evaluate<M, SPL, BM, LEARN, false>(a.NC, ev, T, Mrt, sm, a.r_out ? a.r_out + o0 : nullptr);
+  }
+  double lnl = 0.0;
+  int bad = 0;
+  if (threadIdx.x == 0) {
+    lnl = lnl_total(sm);
+    bad = !isfinite(lnl);
+  }
   const int np = Mrt + Mrt * Mrt + (LEARN ? nb : 0);
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    const float g = grad_of<M, BM, LEARN>(p, Mrt, T, sm);
+    const float g = grad_of<M, SPL, BM, LEARN>(p, Mrt, T, sm);
     bad |= !isfinite(g);
     if (p < Mrt) {
       a.g_mu[(int64_t)b * Mrt + p] = g;
@@ -133,16 +147,110 @@ __global__ void __launch_bounds__(256) k_loglik_grad(LlgArgs a) {
   (void)AP;
 }
 
-template <int M, int SPL, int BM, bool LEARN, bool STAGE>
-__global__ void __launch_bounds__(256) k_fit(FitArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Sm<M> sm;
-  sm.bind(smem, a.carve);
-  constexpr int AP = M + 1;
+// Iterations of one window (events accessed through ev); returns nothing, writes
+// the window's outputs.  See the header's description of the iteration.
+template <int M, int SPL, int BM, bool LEARN, typename EV>
+__device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev, Sm<M> &sm) {
+  constexpr int AP = M + 4;
   const int Mrt = a.Mrt;
   const int nb = BM == 0 ? 1 : Mrt;
   const int np = Mrt + Mrt * Mrt + nb;
   const int nupd = a.fit_beta ? np : Mrt + Mrt * Mrt;
+  const int tid = threadIdx.x;
+  constexpr bool FIXED = std::is_same<EV, EvS>::value && !LEARN && BM == 0;
+  setup_chunks(a.NC, N, T, ev, sm.bnd, sm.anc);
+  if (!LEARN) prepare_states<M, SPL, BM, false>(a.NC, ev, Mrt, sm);
+  if (FIXED) to_decays<M, SPL>(a.NC, sm);
+  const float invN = 1.f / (float)max(N, 1);
+  // convergence bookkeeping lives in thread 0; decisions go through ctl[2]
+  double lnl_prev = 0.0, lnl_out = 0.0;
+  int streak = 0, k = 0;
+  int wst = a.tol > 0.0 ? kE_MAXITER : kOK;
+  float b1t = 1.f, b2t = 1.f;
+  for (k = 0; k < a.max_iters; ++k) {
+    if (LEARN) prepare_states<M, SPL, BM, LEARN>(a.NC, ev, Mrt, sm);
+    evaluate<M, SPL, BM, LEARN, FIXED>(a.NC, ev, T, Mrt, sm, nullptr);
+    int bad = 0;
+    if (tid == 0) {
+      const double val = lnl_total(sm);
+      bad = !isfinite(val);
+      int decision = 0;  // 0 update, 1 stop
+      if (!bad) {
+        if (k > 0 && a.tol > 0.0 && fabs(val - lnl_prev) <= a.tol * fabs(val)) ++streak;
+        else streak = 0;
+        lnl_prev = val;
+        lnl_out = val;
+        if (a.tol > 0.0 && streak >= a.patience) { wst = kOK; decision = 1; }
+        else if (k == a.max_iters - 1) decision = 1;
+      } else if (k == 0) {
+        lnl_out = val;
+      }
+      sm.ctl[2] = decision;
+    }
+    for (int p = tid; p < np; p += blockDim.x) {
+      const float g = grad_of<M, SPL, BM, LEARN>(p, Mrt, T, sm);
+      bad |= !isfinite(g);
+      sm.gbuf[p] = g;
+    }
+    bad = __syncthreads_or(bad);
+    if (bad) {
+      if (k > 0) {
+        for (int p = tid; p < nupd; p += blockDim.x) param_ref<M>(p, Mrt, sm) = sm.prev[p];
+      }
+      wst = kE_NONFINITE;
+      __syncthreads();
+      break;
+    }
+    if (sm.ctl[2]) { ++k; break; }
+    b1t *= a.b1;
+    b2t *= a.b2;
+    for (int p = tid; p < nupd; p += blockDim.x) {
+      const float g = sm.gbuf[p] * invN;
+      float &th = param_ref<M>(p, Mrt, sm);
+      float step;
+      if (a.optimizer == 1) {
+        const float m1 = a.b1 * sm.am[p] + (1.f - a.b1) * g;
+        const float m2 = a.b2 * sm.av[p] + (1.f - a.b2) * g * g;
+        sm.am[p] = m1;
+        sm.av[p] = m2;
+        const float mh = m1 / (1.f - b1t), vh = m2 / (1.f - b2t);
+        step = a.lr * mh / (sqrtf(vh) + a.eps);
+      } else {
+        step = a.lr * g;
+      }
+      const float fl = p < Mrt ? a.mu_floor : (p < Mrt + Mrt * Mrt ? a.alpha_floor : a.beta_floor);
+      sm.prev[p] = th;
+      th = fmaxf(th + step, fl);
+    }
+    __syncthreads();  // the event sums were read; parameters updated
+    clear_accumulators<M, SPL>(sm);
+    if (LEARN) {
+      for (int j = tid; j < M; j += blockDim.x) sm.bl2[j] = sm.beta[j] * kLog2e;
+    }
+    __syncthreads();
+  }
+  // write back the last evaluated point
+  for (int p = tid; p < Mrt * Mrt; p += blockDim.x)
+    a.alpha[(int64_t)b * Mrt * Mrt + p] = sm.alpha[(p / Mrt) * AP + (p % Mrt)];
+  for (int i = tid; i < Mrt; i += blockDim.x) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];
+  for (int j = tid; j < nb; j += blockDim.x) a.beta[(int64_t)b * nb + j] = sm.beta[j];
+  if (tid == 0) {
+    a.loglik[b] = lnl_out;
+    a.iters[b] = k;
+    a.status[b] = wst;
+  }
+  __syncthreads();
+}
+
+template <int M, int SPL, int BM, bool LEARN, bool STAGE>
+__global__ void __launch_bounds__(256, 2) k_fit(FitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Sm<M> sm;
+  sm.bind(smem, a.carve);
+  constexpr int AP = M + 4;
+  const int Mrt = a.Mrt;
+  const int nb = BM == 0 ? 1 : Mrt;
+  const int np = Mrt + Mrt * Mrt + nb;
   const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) sm.ctl[1] = atomicAdd(a.queue, 1);
@@ -176,7 +284,7 @@ __global__ void __launch_bounds__(256) k_fit(FitArgs a) {
     }
     // starting point
     load_params<M, BM>(b, Mrt, a.mu, a.alpha, a.beta, sm);
-    zero_accumulators<M>(sm);
+    clear_accumulators<M, SPL>(sm);
     __syncthreads();
     if (a.init == 1) {  // cold start: mu_i = 0.5 max(N_i,1)/T, alpha_ij = 0.5 beta_ij / M
       for (int p = tid; p < Mrt * Mrt; p += blockDim.x) {
@@ -186,87 +294,20 @@ __global__ void __launch_bounds__(256) k_fit(FitArgs a) {
       for (int i = tid; i < Mrt; i += blockDim.x)
         sm.mu[i] = 0.5f * (float)max(sm.cnt[i], 1) / T;
     }
-    for (int p = tid; p < np; p += blockDim.x) {
-      if (a.optimizer == 1) {
+    if (a.optimizer == 1) {
+      for (int p = tid; p < np; p += blockDim.x) {
         sm.am[p] = 0.f;
         sm.av[p] = 0.f;
       }
     }
     __syncthreads();
-    const float *tt = STAGE ? sm.ev_t : tg;
-    const int16_t *uu = STAGE ? sm.ev_u : ug;
-    const float *ww = wg ? (STAGE ? sm.ev_w : wg) : nullptr;
-    setup_chunks(a.NC, N, T, tt, sm.bnd, sm.anc);
-    if (!LEARN) prepare_states<M, SPL, BM, false>(a.NC, tt, uu, ww, T, Mrt, sm);
-    const float invN = 1.f / (float)max(N, 1);
-    double lnl_prev = 0.0, lnl_out = 0.0;
-    int streak = 0, k = 0;
-    int wst = a.tol > 0.0 ? kE_MAXITER : kOK;
-    float b1t = 1.f, b2t = 1.f;
-    for (k = 0; k < a.max_iters; ++k) {
-      if (LEARN) prepare_states<M, SPL, BM, LEARN>(a.NC, tt, uu, ww, T, Mrt, sm);
-      const double val = evaluate<M, SPL, BM, LEARN>(a.NC, tt, uu, ww, T, Mrt, sm, nullptr);
-      int bad = !isfinite(val);
-      for (int p = tid; p < np; p += blockDim.x) {
-        const float g = grad_of<M, BM, LEARN>(p, Mrt, T, sm);
-        bad |= !isfinite(g);
-        sm.gbuf[p] = g;
-      }
-      bad = __syncthreads_or(bad);
-      if (bad) {
-        if (k > 0) {
-          for (int p = tid; p < nupd; p += blockDim.x) param_ref<M>(p, Mrt, sm) = sm.prev[p];
-        } else {
-          lnl_out = val;
-        }
-        wst = kE_NONFINITE;
-        __syncthreads();
-        break;
-      }
-      if (k > 0 && a.tol > 0.0 && fabs(val - lnl_prev) <= a.tol * fabs(val)) ++streak;
-      else streak = 0;
-      lnl_prev = val;
-      lnl_out = val;
-      if (a.tol > 0.0 && streak >= a.patience) { wst = kOK; ++k; break; }
-      if (k == a.max_iters - 1) { ++k; break; }
-      b1t *= a.b1;
-      b2t *= a.b2;
-      for (int p = tid; p < nupd; p += blockDim.x) {
-        const float g = sm.gbuf[p] * invN;
-        float &th = param_ref<M>(p, Mrt, sm);
-        float step;
-        if (a.optimizer == 1) {
-          const float m1 = a.b1 * sm.am[p] + (1.f - a.b1) * g;
-          const float m2 = a.b2 * sm.av[p] + (1.f - a.b2) * g * g;
-          sm.am[p] = m1;
-          sm.av[p] = m2;
-          const float mh = m1 / (1.f - b1t), vh = m2 / (1.f - b2t);
-          step = a.lr * mh / (sqrtf(vh) + a.eps);
-        } else {
-          step = a.lr * g;
-        }
-        const float fl = p < Mrt ? a.mu_floor : (p < Mrt + Mrt * Mrt ? a.alpha_floor : a.beta_floor);
-        sm.prev[p] = th;
-        th = fmaxf(th + step, fl);
-      }
-      __syncthreads();
-      zero_accumulators<M>(sm);
-      if (LEARN) {
-        for (int j = tid; j < M; j += blockDim.x) sm.bl2[j] = sm.beta[j] * kLog2e;
-      }
-      __syncthreads();
+    if (STAGE) {
+      const EvS ev{sm.ev_t, sm.ev_u, wg ? sm.ev_w : nullptr};
+      fit_window<M, SPL, BM, LEARN>(a, b, N, T, ev, sm);
+    } else {
+      const EvG ev{tg, ug, wg};
+      fit_window<M, SPL, BM, LEARN>(a, b, N, T, ev, sm);
     }
-    // write back the last evaluated point
-    for (int p = tid; p < Mrt * Mrt; p += blockDim.x)
-      a.alpha[(int64_t)b * Mrt * Mrt + p] = sm.alpha[(p / Mrt) * AP + (p % Mrt)];
-    for (int i = tid; i < Mrt; i += blockDim.x) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];
-    for (int j = tid; j < nb; j += blockDim.x) a.beta[(int64_t)b * nb + j] = sm.beta[j];
-    if (tid == 0) {
-      a.loglik[b] = lnl_out;
-      a.iters[b] = k;
-      a.status[b] = wst;
-    }
-    __syncthreads();
   }
 }
 
@@ -311,7 +352,7 @@ __global__ void __launch_bounds__(256) k_weight_grad(WgArgs a) {
     for (int i = 0; i < M; ++i) s += alpha[i * AP + j];
     col[j] = s;
   }
-  setup_chunks(NC, N, T, t, bnd, anc);
+  setup_chunks(NC, N, T, EvG{t, u, nullptr}, bnd, anc);
   const int c = tid;
   float P[M];
   float b2[M];
@@ -331,7 +372,7 @@ __global__ void __launch_bounds__(256) k_weight_grad(WgArgs a) {
       const float dt = tcur - tgp;
       if (dt > 0.f) {
 #pragma unroll
-        for (int j = 0; j < M; ++j) P[j] *= exp2f(-b2[j] * dt);
+        for (int j = 0; j < M; ++j) P[j] *= exp2_acc(-b2[j] * dt);
       }
       tcur = tgp;
       for (int k = gs; k <= n; ++k) {
@@ -345,7 +386,7 @@ __global__ void __launch_bounds__(256) k_weight_grad(WgArgs a) {
     const float dt = tcur - anc[c];
     if (dt > 0.f) {
 #pragma unroll
-      for (int j = 0; j < M; ++j) P[j] *= exp2f(-b2[j] * dt);
+      for (int j = 0; j < M; ++j) P[j] *= exp2_acc(-b2[j] * dt);
     }
 #pragma unroll
     for (int j = 0; j < M; ++j) enc[c * M + j] = P[j];
@@ -359,7 +400,7 @@ __global__ void __launch_bounds__(256) k_weight_grad(WgArgs a) {
       const float loc = enc[cc * M + j];
       enc[cc * M + j] = E;
       const float D = anc[cc + 1] - anc[cc];
-      E = fmaf(exp2f(-bl2[j] * D), E, loc);
+      E = fmaf(exp2_acc(-bl2[j] * D), E, loc);
     }
   }
   __syncthreads();
@@ -377,7 +418,7 @@ __global__ void __launch_bounds__(256) k_weight_grad(WgArgs a) {
       const float dt = tcur - tgp;
       if (dt > 0.f) {
 #pragma unroll
-        for (int j = 0; j < M; ++j) P[j] *= exp2f(-b2[j] * dt);
+        for (int j = 0; j < M; ++j) P[j] *= exp2_acc(-b2[j] * dt);
       }
       tcur = tgp;
       for (int k = gs; k <= n; ++k) {

@@ -15,16 +15,22 @@
 //   * the CTA's threads form NC = blockDim / SPL chunk groups; chunk c owns the
 //     contiguous events [b_c, b_{c+1}), boundaries moved past tie groups so that
 //     a timestamp never straddles two chunks;
-//   * SPL threads of a chunk split the M sources (MS = M / SPL each), so the
-//     per-thread state R[MS] (and S[MS]) lives in registers;
+//   * SPL threads of a chunk split the M sources (MS = M / SPL each, a multiple
+//     of 4 so rows move as float4), so the per-thread state R[MS] (and S[MS])
+//     lives in registers;
 //   * pass 1 computes each chunk's local effect (state at the next chunk's
 //     anchor, starting from zero), a per-source scan over chunks composes the
 //     affine maps (R, S) -> (A R + R_loc, A (S + D R) + S_loc), A = exp(-beta D),
 //     and gives every chunk its entering state; with fixed beta this runs once
 //     per window, with learned beta once per evaluation;
 //   * pass 2 walks each chunk from its entering state and accumulates ln lambda
-//     (Kahan, FP32), d/dmu and d/dalpha (shared-memory atomics) and d/dbeta
-//     (registers).
+//     (Kahan, FP32), d/dmu and d/dalpha and d/dbeta.  The d/dalpha row of an
+//     event is selected by its id, which differs from lane to lane; it is
+//     accumulated without atomics in per-thread private slots laid out
+//     [id][float4 slice][thread] (conflict-free: a warp's 32 lanes always hit 32
+//     distinct 16-byte slots in consecutive banks), and summed over threads
+//     once per evaluation.  For M = 64 the private slots would not fit, and the
+//     sums go to one shared copy with shared-memory atomics instead.
 // Ties (Sec. II: the inner sum is strict): the increments of a tie group are
 // added only when time advances past it.
 #pragma once
@@ -42,6 +48,34 @@ enum : int {
   kE_NONFINITE = 5, kE_MAXITER = 6
 };
 
+// private accumulators for template capacity M (atomics beyond)
+template <int M>
+struct UsePriv {
+  static constexpr bool value = M <= 32;
+};
+
+// 2^x for the decay factors of the recursion.  x = k + f with k = rint(x) and
+// |f| <= 1/2; 2^f from its Taylor series e^(f ln 2) to degree 7 (truncation
+// below 6e-9 relative), evaluated by Horner so the last rounding is a plain
+// round-to-nearest; 2^k applied exactly through the exponent field.  Unlike
+// the approximate hardware exponential its error has no one-sided bias, which
+// matters because the recursion multiplies thousands of these factors.
+__device__ __forceinline__ float exp2_acc(float x) {
+  const float xc = fmaxf(x, -125.f);
+  const float k = rintf(xc);
+  const float f = xc - k;
+  float p = 1.5252733804059840e-05f;
+  p = fmaf(p, f, 1.5403530393381608e-04f);
+  p = fmaf(p, f, 1.3333558146428443e-03f);
+  p = fmaf(p, f, 9.6181291076284772e-03f);
+  p = fmaf(p, f, 5.5504108664821580e-02f);
+  p = fmaf(p, f, 2.4022650695910071e-01f);
+  p = fmaf(p, f, 6.9314718055994531e-01f);
+  p = fmaf(p, f, 1.0f);
+  const float r = p * __int_as_float(((int)k + 127) << 23);
+  return x < -125.f ? 0.f : r;
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   const float y = x - c;
   const float t = s + y;
@@ -49,46 +83,78 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   s = t;
 }
 
+// ---------------------------------------------------------------------------
+// Event access: staged in shared memory (t float, id uint16: 6 bytes per
+// event) or read from global memory.
+// ---------------------------------------------------------------------------
+struct EvS {
+  const float *t;
+  const uint16_t *u;
+  const float *w;
+  __device__ __forceinline__ void get(int n, float &tt, int &uu) const {
+    tt = t[n];
+    uu = (int)u[n];
+  }
+  __device__ __forceinline__ float time(int n) const { return t[n]; }
+  __device__ __forceinline__ int id(int n) const { return (int)u[n]; }
+  __device__ __forceinline__ float wt(int n) const { return w ? w[n] : 1.f; }
+};
+
+struct EvG {
+  const float *t;
+  const int16_t *u;
+  const float *w;
+  __device__ __forceinline__ void get(int n, float &tt, int &uu) const {
+    tt = __ldg(t + n);
+    uu = (int)__ldg(u + n);
+  }
+  __device__ __forceinline__ float time(int n) const { return __ldg(t + n); }
+  __device__ __forceinline__ int id(int n) const { return (int)__ldg(u + n); }
+  __device__ __forceinline__ float wt(int n) const { return w ? __ldg(w + n) : 1.f; }
+};
+
 // First event of chunk c out of NC over [0, N): the even split moved forward
 // past any tie group, so every chunk starts at a new timestamp.
-template <typename TP>
-__device__ __forceinline__ int chunk_begin(int c, int NC, int N, TP t) {
+template <typename EV>
+__device__ __forceinline__ int chunk_begin(int c, int NC, int N, const EV &ev) {
   if (c >= NC) return N;
   int b = (int)(((long long)c * (long long)N) / NC);
-  while (b > 0 && b < N && t[b] == t[b - 1]) ++b;
+  while (b > 0 && b < N && ev.time(b) == ev.time(b - 1)) ++b;
   return b;
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory carve of one CTA (sizes depend on M, NC, event capacity).
+// Shared-memory carve of one CTA (sizes depend on M, NT, NC, event capacity).
 // ---------------------------------------------------------------------------
 struct Carve {
   // byte offsets
-  int alpha, ga, mu, gm, beta, bl2, gb, W, cnt, C, dC, endR, endS, anc, bnd, encR, encS, prev,
-      gbuf, am, av, red, ctl, ev_t, ev_u, ev_w;
+  int alpha, oh, ga, mu, gm, beta, bl2, gb, W, cnt, C, dC, endR, endS, anc, bnd, encR, encS, prev,
+      gbuf, am, av, red, ctl, gpriv, mpriv, ev_t, ev_u, ev_w;
   int total;
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int pitch4(int M) { return M + 4; }  // 16-byte rows, staggered banks
 
-// np_max = M + M*M + M parameters.
-__host__ __device__ inline Carve make_carve(int M, int NC, int ev_cap, bool weights, bool learn,
-                                            bool adam, bool fit) {
+__host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, bool weights,
+                                            bool learn, bool adam, bool fit, bool priv) {
+  const int NC = NT / SPL;
   Carve c;
   int o = 0;
-  const int AP = M + 1;
+  const int AP = pitch4(M);
   const int npm = M + M * M + M;
   auto take = [&](int bytes) { int r = o; o = align_up(o + bytes, 16); return r; };
   c.red = take(32 * 8);
   c.ctl = take(16 * 4);
   c.alpha = take(M * AP * 4);
-  c.ga = take(M * AP * 4);
+  c.oh = take(M * AP * 4);
+  c.ga = priv ? 0 : take(M * (M + 1) * 4);
   c.mu = take(M * 4);
   c.gm = take(M * 4);
   c.beta = take(M * 4);
   c.bl2 = take(M * 4);
   c.gb = take(M * 4);
-  c.W = take(M * 4);
+  c.W = take(M * 8);
   c.cnt = take(M * 4);
   c.C = take(M * 4);
   c.dC = take(M * 4);
@@ -102,6 +168,8 @@ __host__ __device__ inline Carve make_carve(int M, int NC, int ev_cap, bool weig
   c.gbuf = fit ? take(npm * 4) : 0;
   c.am = (fit && adam) ? take(npm * 4) : 0;
   c.av = (fit && adam) ? take(npm * 4) : 0;
+  c.gpriv = priv ? take(M * (M / SPL) * NT * 4) : 0;  // [id][slice][thread] float4
+  c.mpriv = priv ? take(M * NC * 4) : 0;                // [id][chunk]
   c.ev_t = ev_cap > 0 ? take(ev_cap * 4) : 0;
   c.ev_w = (ev_cap > 0 && weights) ? take(ev_cap * 4) : 0;
   c.ev_u = ev_cap > 0 ? take(ev_cap * 2) : 0;
@@ -109,40 +177,34 @@ __host__ __device__ inline Carve make_carve(int M, int NC, int ev_cap, bool weig
   return c;
 }
 
-// Everything a CTA needs about its current window.
-struct WinCtx {
-  const float *t;      // events (shared or global)
-  const int16_t *u;
-  const float *w;      // nullptr => weight 1
-  int N;
-  float T;
-  int Mrt;             // runtime number of types (<= M)
-};
-
 template <int M>
 struct Sm {
-  float *alpha, *ga, *mu, *gm, *beta, *bl2, *gb, *W, *C, *dC, *endR, *endS, *anc, *encR, *encS,
-      *prev, *gbuf, *am, *av;
+  double *W;  // per-type weight sums (exact for counts, FP64 for weights)
+  float *alpha, *oh, *ga, *mu, *gm, *beta, *bl2, *gb, *C, *dC, *endR, *endS, *anc, *encR,
+      *encS, *prev, *gbuf, *am, *av, *gpriv, *mpriv;
   int *bnd, *cnt, *ctl;
   double *red;
   float *ev_t, *ev_w;
-  int16_t *ev_u;
+  uint16_t *ev_u;
   __device__ void bind(unsigned char *base, const Carve &c) {
-    alpha = (float *)(base + c.alpha); ga = (float *)(base + c.ga); mu = (float *)(base + c.mu);
-    gm = (float *)(base + c.gm); beta = (float *)(base + c.beta); bl2 = (float *)(base + c.bl2);
-    gb = (float *)(base + c.gb); W = (float *)(base + c.W); cnt = (int *)(base + c.cnt);
-    C = (float *)(base + c.C); dC = (float *)(base + c.dC); endR = (float *)(base + c.endR);
-    endS = (float *)(base + c.endS); anc = (float *)(base + c.anc); bnd = (int *)(base + c.bnd);
+    alpha = (float *)(base + c.alpha); oh = (float *)(base + c.oh); ga = (float *)(base + c.ga);
+    mu = (float *)(base + c.mu); gm = (float *)(base + c.gm); beta = (float *)(base + c.beta);
+    bl2 = (float *)(base + c.bl2); gb = (float *)(base + c.gb); W = (double *)(base + c.W);
+    cnt = (int *)(base + c.cnt); C = (float *)(base + c.C); dC = (float *)(base + c.dC);
+    endR = (float *)(base + c.endR); endS = (float *)(base + c.endS);
+    anc = (float *)(base + c.anc); bnd = (int *)(base + c.bnd);
     encR = (float *)(base + c.encR); encS = (float *)(base + c.encS);
-    prev = (float *)(base + c.prev); gbuf = (float *)(base + c.gbuf); am = (float *)(base + c.am); av = (float *)(base + c.av);
+    prev = (float *)(base + c.prev); gbuf = (float *)(base + c.gbuf);
+    am = (float *)(base + c.am); av = (float *)(base + c.av);
+    gpriv = (float *)(base + c.gpriv); mpriv = (float *)(base + c.mpriv);
     red = (double *)(base + c.red); ctl = (int *)(base + c.ctl);
     ev_t = (float *)(base + c.ev_t); ev_w = (float *)(base + c.ev_w);
-    ev_u = (int16_t *)(base + c.ev_u);
+    ev_u = (uint16_t *)(base + c.ev_u);
   }
 };
 
 // ---------------------------------------------------------------------------
-// Block reductions
+// Block reduction (every thread receives the same sum, in the same order)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double block_sum_double(double v, double *red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -151,26 +213,23 @@ __device__ __forceinline__ double block_sum_double(double v, double *red) {
   if (lane == 0) red[wid] = v;
   __syncthreads();
   double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];  // every thread gets the same order
+  for (int i = 0; i < nw; ++i) s += red[i];
   return s;
 }
 
 // ---------------------------------------------------------------------------
-// Per-thread recursion pieces.  MS sources starting at `base`.
+// Per-thread recursion over MS sources starting at `base` (MS % 4 == 0).
 // ---------------------------------------------------------------------------
 template <int MS, int BM, bool LEARN>
 struct Walker {
+  static_assert(MS % 4 == 0, "sources per thread must be a multiple of 4");
   float R[MS];
   float S[LEARN ? MS : 1];
   float b2[BM == 0 ? 1 : MS];  // beta * log2(e)
 
   __device__ __forceinline__ void load_beta(const float *bl2, int base) {
-    if (BM == 0) {
-      b2[0] = bl2[0];
-    } else {
 #pragma unroll
-      for (int jj = 0; jj < (BM == 0 ? 1 : MS); ++jj) b2[jj] = bl2[base + jj];
-    }
+    for (int jj = 0; jj < (BM == 0 ? 1 : MS); ++jj) b2[jj] = bl2[BM == 0 ? 0 : base + jj];
   }
   __device__ __forceinline__ void zero() {
 #pragma unroll
@@ -181,7 +240,7 @@ struct Walker {
   }
   __device__ __forceinline__ void decay(float dt) {
     if (BM == 0) {
-      const float a = exp2f(-b2[0] * dt);
+      const float a = exp2_acc(-b2[0] * dt);
 #pragma unroll
       for (int jj = 0; jj < MS; ++jj) {
         if (LEARN) S[jj] = a * fmaf(dt, R[jj], S[jj]);
@@ -190,131 +249,166 @@ struct Walker {
     } else {
 #pragma unroll
       for (int jj = 0; jj < MS; ++jj) {
-        const float a = exp2f(-b2[(BM == 0) ? 0 : jj] * dt);
+        const float a = exp2_acc(-b2[BM == 0 ? 0 : jj] * dt);
         if (LEARN) S[jj] = a * fmaf(dt, R[jj], S[jj]);
         R[jj] *= a;
       }
     }
   }
-  // add the increments of events [k0, k1) (a finished tie group)
-  template <typename TP, typename UP, typename WP>
-  __device__ __forceinline__ void add_events(int k0, int k1, TP, UP u, WP w, int base) {
-    for (int k = k0; k < k1; ++k) {
-      const int uk = (int)u[k] - base;
-      const float wk = w ? w[k] : 1.f;
+  // R += w * e_u restricted to my sources: one row of the identity table
+  __device__ __forceinline__ void add(const float *oh_row, float w) {
+    const float4 *o4 = reinterpret_cast<const float4 *>(oh_row);
 #pragma unroll
-      for (int jj = 0; jj < MS; ++jj) R[jj] += (uk == jj) ? wk : 0.f;
+    for (int q = 0; q < MS / 4; ++q) {
+      const float4 o = o4[q];
+      R[4 * q + 0] = fmaf(o.x, w, R[4 * q + 0]);
+      R[4 * q + 1] = fmaf(o.y, w, R[4 * q + 1]);
+      R[4 * q + 2] = fmaf(o.z, w, R[4 * q + 2]);
+      R[4 * q + 3] = fmaf(o.w, w, R[4 * q + 3]);
     }
   }
 };
 
 // Pass 1 for chunk [b0, b1) anchored at a0, ending at a1: local state -> encR/encS[c].
-template <int M, int SPL, int BM, bool LEARN, typename TP, typename UP, typename WP>
+template <int M, int SPL, int BM, bool LEARN, typename EV>
 __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float a0, float a1,
-                                            TP t, UP u, WP w, const float *bl2, float *encR,
-                                            float *encS) {
+                                            const EV &ev, const Sm<M> &sm) {
   constexpr int MS = M / SPL;
+  constexpr int AP = M + 4;
   const int base = s * MS;
   Walker<MS, BM, LEARN> wk;
-  wk.load_beta(bl2, base);
+  wk.load_beta(sm.bl2, base);
   wk.zero();
   float tprev = a0;
   int gs = b0;
   for (int n = b0; n < b1; ++n) {
-    const float tn = t[n];
+    const float tn = ev.time(n);
     if (tn > tprev) {
-      wk.add_events(gs, n, t, u, w, base);
+      for (int k = gs; k < n; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
       wk.decay(tn - tprev);
       tprev = tn;
       gs = n;
     }
   }
-  wk.add_events(gs, b1, t, u, w, base);
+  for (int k = gs; k < b1; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
   if (a1 > tprev) wk.decay(a1 - tprev);
 #pragma unroll
   for (int jj = 0; jj < MS; ++jj) {
-    encR[c * M + base + jj] = wk.R[jj];
-    if (LEARN) encS[c * M + base + jj] = wk.S[jj];
+    sm.encR[c * M + base + jj] = wk.R[jj];
+    if (LEARN) sm.encS[c * M + base + jj] = wk.S[jj];
   }
 }
 
 // Per-source scan over chunks: encR/encS[c] become entering states; end state
 // (at T_span, all events included) goes to endR/endS.  Threads j < M.
-template <int M, bool LEARN>
-__device__ __forceinline__ void scan_chunks(int NC, const float *anc, const float *bl2, int bm,
-                                            float *encR, float *encS, float *endR, float *endS) {
+template <int M, int BM, bool LEARN>
+__device__ __forceinline__ void scan_chunks(int NC, const Sm<M> &sm) {
   const int j = threadIdx.x;
   if (j >= M) return;
-  const float b = bl2[bm == 0 ? 0 : j];
+  const float b = sm.bl2[BM == 0 ? 0 : j];
   float R = 0.f, S = 0.f;
   for (int c = 0; c < NC; ++c) {
-    const float lr = encR[c * M + j];
-    const float ls = LEARN ? encS[c * M + j] : 0.f;
-    encR[c * M + j] = R;
-    if (LEARN) encS[c * M + j] = S;
-    const float D = anc[c + 1] - anc[c];
-    const float A = exp2f(-b * D);
+    const float lr = sm.encR[c * M + j];
+    const float ls = LEARN ? sm.encS[c * M + j] : 0.f;
+    sm.encR[c * M + j] = R;
+    if (LEARN) sm.encS[c * M + j] = S;
+    const float D = sm.anc[c + 1] - sm.anc[c];
+    const float A = exp2_acc(-b * D);
     if (LEARN) S = fmaf(A, fmaf(D, R, S), ls);
     R = fmaf(A, R, lr);
   }
-  endR[j] = R;
-  if (LEARN) endS[j] = S;
+  sm.endR[j] = R;
+  if (LEARN) sm.endS[j] = S;
 }
 
-// Pass 2 for chunk c: lnL (log2 units, Kahan), atomics into gm/ga, beta grads in gbl.
-template <int M, int SPL, int BM, bool LEARN, typename TP, typename UP, typename WP>
-__device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float a0, TP t, UP u,
-                                            WP w, const float *bl2, const float *encR,
-                                            const float *encS, const float *alpha, const float *mu,
-                                            float *ga, float *gm, float &Ls, float &Lc,
+// Pass 2 for chunk c: lnL (log2 units, Kahan), d/dmu, d/dalpha, d/dbeta.
+template <int M, int SPL, int BM, bool LEARN, typename EV>
+__device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float a0, const EV &ev,
+                                            const Sm<M> &sm, float &Ls, float &Lc,
                                             float (&gbl)[LEARN ? M / SPL : 1], float *r_out) {
   constexpr int MS = M / SPL;
-  constexpr int AP = M + 1;
+  constexpr int NQ = MS / 4;
+  constexpr int AP = M + 4;
+  constexpr bool PRIV = UsePriv<M>::value;
   const int base = s * MS;
-  const int lane = threadIdx.x & 31;
-  const unsigned gmask = (SPL == 32) ? 0xffffffffu
-                                     : (((1u << SPL) - 1u) << (lane & ~(SPL - 1)));
+  const int tid = threadIdx.x;
+  const int NT = blockDim.x;
+  const int lane = tid & 31;
+  const unsigned gmask = (SPL >= 32) ? 0xffffffffu : (((1u << SPL) - 1u) << (lane & ~(SPL - 1)));
   Walker<MS, BM, LEARN> wk;
-  wk.load_beta(bl2, base);
+  wk.load_beta(sm.bl2, base);
 #pragma unroll
   for (int jj = 0; jj < MS; ++jj) {
-    wk.R[jj] = encR[c * M + base + jj];
-    if (LEARN) wk.S[jj] = encS[c * M + base + jj];
+    wk.R[jj] = sm.encR[c * M + base + jj];
+    if (LEARN) wk.S[jj] = sm.encS[c * M + base + jj];
   }
+  float4 *gp = reinterpret_cast<float4 *>(sm.gpriv);
   float tprev = a0;
   int gs = b0;
+  int pu = 0;
+  float pw = 0.f;
   for (int n = b0; n < b1; ++n) {
-    const float tn = t[n];
-    const int un = (int)u[n];
+    float tn;
+    int un;
+    ev.get(n, tn, un);
     if (tn > tprev) {
-      wk.add_events(gs, n, t, u, w, base);
+      if (n - gs == 1) {
+        wk.add(sm.oh + pu * AP + base, pw);
+      } else {
+        for (int k = gs; k < n; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
+      }
       wk.decay(tn - tprev);
       tprev = tn;
       gs = n;
     }
-    const float *arow = alpha + un * AP + base;
-    float av[MS];
-    float dot = 0.f;
+    pu = un;
+    pw = ev.wt(n);
+    const float4 *arow = reinterpret_cast<const float4 *>(sm.alpha + un * AP + base);
+    float4 av[NQ];
+    float d0 = 0.f, d1 = 0.f;
 #pragma unroll
-    for (int jj = 0; jj < MS; ++jj) {
-      av[jj] = arow[jj];
-      dot = fmaf(av[jj], wk.R[jj], dot);
+    for (int q = 0; q < NQ; ++q) {
+      av[q] = arow[q];
+      d0 = fmaf(av[q].x, wk.R[4 * q + 0], d0);
+      d1 = fmaf(av[q].y, wk.R[4 * q + 1], d1);
+      d0 = fmaf(av[q].z, wk.R[4 * q + 2], d0);
+      d1 = fmaf(av[q].w, wk.R[4 * q + 3], d1);
     }
+    float dot = d0 + d1;
 #pragma unroll
     for (int o = 1; o < SPL; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
-    const float lam = mu[un] + dot;
-    const float r = __frcp_rn(lam);
+    const float lam = sm.mu[un] + dot;
+    const float r = __fdividef(1.f, lam);
     if (s == 0) {
       kahan_add(Ls, Lc, __log2f(lam));
-      atomicAdd(&gm[un], r);
+      if (PRIV) sm.mpriv[un * (NT / SPL) + c] += r;
+      else atomicAdd(&sm.gm[un], r);
       if (r_out) r_out[n] = r;
     }
-    float *grow = ga + un * AP + base;
+    if (PRIV) {
+      float4 *g = gp + (un * NQ) * NT + tid;
 #pragma unroll
-    for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[jj], r * wk.R[jj]);
+      for (int q = 0; q < NQ; ++q) {
+        float4 x = g[q * NT];
+        x.x = fmaf(r, wk.R[4 * q + 0], x.x);
+        x.y = fmaf(r, wk.R[4 * q + 1], x.y);
+        x.z = fmaf(r, wk.R[4 * q + 2], x.z);
+        x.w = fmaf(r, wk.R[4 * q + 3], x.w);
+        g[q * NT] = x;
+      }
+    } else {
+      float *grow = sm.ga + un * (M + 1) + base;
+#pragma unroll
+      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[jj], r * wk.R[jj]);
+    }
     if (LEARN) {
 #pragma unroll
-      for (int jj = 0; jj < MS; ++jj) gbl[jj] = fmaf(-r * av[jj], wk.S[jj], gbl[jj]);
+      for (int q = 0; q < NQ; ++q) {
+        gbl[4 * q + 0] = fmaf(-r * av[q].x, wk.S[4 * q + 0], gbl[4 * q + 0]);
+        gbl[4 * q + 1] = fmaf(-r * av[q].y, wk.S[4 * q + 1], gbl[4 * q + 1]);
+        gbl[4 * q + 2] = fmaf(-r * av[q].z, wk.S[4 * q + 2], gbl[4 * q + 2]);
+        gbl[4 * q + 3] = fmaf(-r * av[q].w, wk.S[4 * q + 3], gbl[4 * q + 3]);
+      }
     }
   }
 }
@@ -332,7 +426,7 @@ __device__ int stage_and_validate(const float *tg, const int16_t *ug, const floa
   if (tid == 0) sm.ctl[0] = 0x7fffffff;
   for (int j = tid; j < M; j += nt) {
     sm.cnt[j] = 0;
-    sm.W[j] = 0.f;
+    sm.W[j] = 0.0;
   }
   __syncthreads();
   int code = 0x7fffffff;
@@ -347,49 +441,59 @@ __device__ int stage_and_validate(const float *tg, const int16_t *ug, const floa
     if (n > 0 && tv < tg[n - 1]) code = min(code, (int)kE_UNSORTED);
     if (STAGE) {
       sm.ev_t[n] = tv;
-      sm.ev_u[n] = (int16_t)uv;
+      sm.ev_u[n] = (uint16_t)uv;
       if (wg) sm.ev_w[n] = wv;
     }
     if (uv >= 0 && uv < Mrt) {
       atomicAdd(&sm.cnt[uv], 1);
-      atomicAdd(&sm.W[uv], wv);
+      if (wg) atomicAdd(&sm.W[uv], (double)wv);
     }
   }
   if (code != 0x7fffffff) atomicMin(&sm.ctl[0], code);
+  __syncthreads();
+  if (!wg)
+    for (int j = tid; j < M; j += nt) sm.W[j] = (double)sm.cnt[j];
   __syncthreads();
   const int st = sm.ctl[0];
   return st == 0x7fffffff ? kOK : st;
 }
 
 // Chunk boundaries and anchors (a_c = first time of chunk c, T for an empty tail).
-template <typename TP>
-__device__ void setup_chunks(int NC, int N, float T, TP t, int *bnd, float *anc) {
+template <typename EV>
+__device__ void setup_chunks(int NC, int N, float T, const EV &ev, int *bnd, float *anc) {
   for (int c = threadIdx.x; c <= NC; c += blockDim.x) {
-    const int b = chunk_begin(c, NC, N, t);
+    const int b = chunk_begin(c, NC, N, ev);
     bnd[c] = b;
-    anc[c] = (c < NC && b < N) ? t[b] : T;
+    anc[c] = (c < NC && b < N) ? ev.time(b) : T;
   }
   __syncthreads();
 }
 
+// Identity table used for the increments (rows padded to the alpha pitch).
+template <int M>
+__device__ void fill_onehot(Sm<M> &sm) {
+  constexpr int AP = M + 4;
+  for (int p = threadIdx.x; p < M * AP; p += blockDim.x) sm.oh[p] = (p / AP == p % AP) ? 1.f : 0.f;
+}
+
 // Pass 1 + scan + compensator constants.  Leaves C, dC, endR, endS in smem.
-template <int M, int SPL, int BM, bool LEARN, typename TP, typename UP, typename WP>
-__device__ void prepare_states(int NC, TP t, UP u, WP w, float T, int Mrt, Sm<M> &sm) {
+template <int M, int SPL, int BM, bool LEARN, typename EV>
+__device__ void prepare_states(int NC, const EV &ev, int Mrt, Sm<M> &sm) {
   const int tid = threadIdx.x;
   const int c = tid / SPL, s = tid % SPL;
   if (c < NC) {
-    pass1_chunk<M, SPL, BM, LEARN>(c, s, sm.bnd[c], sm.bnd[c + 1], sm.anc[c], sm.anc[c + 1], t, u,
-                                   w, sm.bl2, sm.encR, sm.encS);
+    pass1_chunk<M, SPL, BM, LEARN>(c, s, sm.bnd[c], sm.bnd[c + 1], sm.anc[c], sm.anc[c + 1], ev,
+                                   sm);
   }
   __syncthreads();
-  scan_chunks<M, LEARN>(NC, sm.anc, sm.bl2, BM, sm.encR, sm.encS, sm.endR, sm.endS);
+  scan_chunks<M, BM, LEARN>(NC, sm);
   __syncthreads();
   for (int j = tid; j < M; j += blockDim.x) {
     if (j < Mrt) {
-      const float b = sm.beta[BM == 0 ? 0 : j];
-      const float Cj = (sm.W[j] - sm.endR[j]) / b;
-      sm.C[j] = Cj;
-      sm.dC[j] = LEARN ? (sm.endS[j] - Cj) / b : 0.f;
+      const double b = (double)sm.beta[BM == 0 ? 0 : j];
+      const double Cj = (sm.W[j] - (double)sm.endR[j]) / b;
+      sm.C[j] = (float)Cj;
+      sm.dC[j] = LEARN ? (float)(((double)sm.endS[j] - Cj) / b) : 0.f;
     } else {
       sm.C[j] = 0.f;
       sm.dC[j] = 0.f;
@@ -398,13 +502,144 @@ __device__ void prepare_states(int NC, TP t, UP u, WP w, float T, int Mrt, Sm<M>
   __syncthreads();
 }
 
-// One lnL + gradient evaluation at the parameters in smem.  On return (after
-// a barrier) ga/gm/gb hold the event sums, and the returned double is lnL
-// (identical on every thread).  r_out: optional 1/lambda per event (global).
-template <int M, int SPL, int BM, bool LEARN, typename TP, typename UP, typename WP>
-__device__ double evaluate(int NC, TP t, UP u, WP w, float T, int Mrt, Sm<M> &sm, float *r_out) {
+// Clear the accumulators pass 2 writes (own private slots, or the shared copy).
+template <int M, int SPL>
+__device__ __forceinline__ void clear_accumulators(Sm<M> &sm) {
+  constexpr int NQ = M / SPL / 4;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  if (UsePriv<M>::value) {
+    float4 *gp = reinterpret_cast<float4 *>(sm.gpriv);
+    for (int u = 0; u < M; ++u) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) gp[(u * NQ + q) * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int p = tid; p < M * (NT / SPL); p += NT) sm.mpriv[p] = 0.f;
+  } else {
+    for (int p = tid; p < M * (M + 1); p += NT) sm.ga[p] = 0.f;
+    for (int j = tid; j < M; j += NT) sm.gm[j] = 0.f;
+  }
+  for (int j = tid; j < M; j += NT) sm.gb[j] = 0.f;
+}
+
+// Fixed scalar beta, staged events: replace each staged time by the decay
+// factor from the previous event, exp(-beta (t_n - t_{n-1})), and mark the
+// first event of every tie group in bit 15 of its id.  One thread per chunk;
+// a chunk's first event starts from the entering state and needs no factor.
+// Runs once per window, after pass 1 (which still needs the times).
+template <int M, int SPL>
+__device__ void to_decays(int NC, Sm<M> &sm) {
+  const int tid = threadIdx.x;
+  const int c = tid / SPL, s = tid % SPL;
+  if (c < NC && s == 0) {
+    const int b0 = sm.bnd[c], b1 = sm.bnd[c + 1];
+    const float b2 = sm.bl2[0];
+    float tprev = (b0 < b1) ? sm.ev_t[b0] : 0.f;
+    for (int n = b0; n < b1; ++n) {
+      const float tn = sm.ev_t[n];
+      const float dt = tn - tprev;
+      sm.ev_t[n] = exp2_acc(-b2 * dt);
+      if (dt > 0.f) sm.ev_u[n] = (uint16_t)(sm.ev_u[n] | 0x8000u);
+      tprev = tn;
+    }
+  }
+  __syncthreads();
+}
+
+// Pass 2 with precomputed decay factors (fixed scalar beta, staged events).
+template <int M, int SPL>
+__device__ __forceinline__ void pass2_fixed(int c, int s, int b0, int b1, const float *w,
+                                            const Sm<M> &sm, float &Ls, float &Lc, float *r_out) {
   constexpr int MS = M / SPL;
-  constexpr int AP = M + 1;
+  constexpr int NQ = MS / 4;
+  constexpr int AP = M + 4;
+  constexpr bool PRIV = UsePriv<M>::value;
+  const int base = s * MS;
+  const int tid = threadIdx.x;
+  const int NT = blockDim.x;
+  const int lane = tid & 31;
+  const unsigned gmask = (SPL >= 32) ? 0xffffffffu : (((1u << SPL) - 1u) << (lane & ~(SPL - 1)));
+  const float *A = sm.ev_t;
+  const uint16_t *U = sm.ev_u;
+  Walker<MS, 0, false> wk;
+#pragma unroll
+  for (int jj = 0; jj < MS; ++jj) wk.R[jj] = sm.encR[c * M + base + jj];
+  float4 *gp = reinterpret_cast<float4 *>(sm.gpriv);
+  int gs = b0;
+  int pu = 0;
+  float pw = 0.f;
+  for (int n = b0; n < b1; ++n) {
+    const float an = A[n];
+    const int cd = (int)U[n];
+    const int un = cd & 0x7fff;
+    if (cd & 0x8000) {
+      if (n - gs == 1) {
+        wk.add(sm.oh + pu * AP + base, pw);
+      } else {
+        for (int k = gs; k < n; ++k) wk.add(sm.oh + ((int)U[k] & 0x7fff) * AP + base, w ? w[k] : 1.f);
+      }
+#pragma unroll
+      for (int jj = 0; jj < MS; ++jj) wk.R[jj] *= an;
+      gs = n;
+    }
+    pu = un;
+    pw = w ? w[n] : 1.f;
+    const float4 *arow = reinterpret_cast<const float4 *>(sm.alpha + un * AP + base);
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const float4 av = arow[q];
+      d0 = fmaf(av.x, wk.R[4 * q + 0], d0);
+      d1 = fmaf(av.y, wk.R[4 * q + 1], d1);
+      d0 = fmaf(av.z, wk.R[4 * q + 2], d0);
+      d1 = fmaf(av.w, wk.R[4 * q + 3], d1);
+    }
+    float dot = d0 + d1;
+#pragma unroll
+    for (int o = 1; o < SPL; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
+    const float lam = sm.mu[un] + dot;
+    const float r = __fdividef(1.f, lam);
+    if (s == 0) {
+      kahan_add(Ls, Lc, __log2f(lam));
+      if (PRIV) sm.mpriv[un * (NT / SPL) + c] += r;
+      else atomicAdd(&sm.gm[un], r);
+      if (r_out) r_out[n] = r;
+    }
+    if (PRIV) {
+      float4 *g = gp + (un * NQ) * NT + tid;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        float4 x = g[q * NT];
+        x.x = fmaf(r, wk.R[4 * q + 0], x.x);
+        x.y = fmaf(r, wk.R[4 * q + 1], x.y);
+        x.z = fmaf(r, wk.R[4 * q + 2], x.z);
+        x.w = fmaf(r, wk.R[4 * q + 3], x.w);
+        g[q * NT] = x;
+      }
+    } else {
+      float *grow = sm.ga + un * (M + 1) + base;
+#pragma unroll
+      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[jj], r * wk.R[jj]);
+    }
+  }
+}
+
+// Error-free sum of two floats added into a (hi, lo) pair.
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
+// One lnL + gradient evaluation at the parameters in smem.  The accumulators
+// must be clear.  On return (after a barrier) the event sums are complete and
+// each warp's compensated partial sums of Part1 (log2 units) and of Part2 +
+// Part3 sit in red as float4 (hi1, lo1, hi23, lo23); lnl_total() adds them up.
+// FIXED: staged events already converted by to_decays (fixed scalar beta).
+template <int M, int SPL, int BM, bool LEARN, bool FIXED, typename EV>
+__device__ void evaluate(int NC, const EV &ev, float T, int Mrt, Sm<M> &sm, float *r_out) {
+  constexpr int MS = M / SPL;
+  constexpr int AP = M + 4;
   const int tid = threadIdx.x;
   const int c = tid / SPL, s = tid % SPL;
   float Ls = 0.f, Lc = 0.f;
@@ -412,9 +647,12 @@ __device__ double evaluate(int NC, TP t, UP u, WP w, float T, int Mrt, Sm<M> &sm
 #pragma unroll
   for (int jj = 0; jj < (LEARN ? MS : 1); ++jj) gbl[jj] = 0.f;
   if (c < NC) {
-    pass2_chunk<M, SPL, BM, LEARN>(c, s, sm.bnd[c], sm.bnd[c + 1], sm.anc[c], t, u, w, sm.bl2,
-                                   sm.encR, sm.encS, sm.alpha, sm.mu, sm.ga, sm.gm, Ls, Lc, gbl,
-                                   r_out);
+    if (FIXED) {
+      pass2_fixed<M, SPL>(c, s, sm.bnd[c], sm.bnd[c + 1], ev.w, sm, Ls, Lc, r_out);
+    } else {
+      pass2_chunk<M, SPL, BM, LEARN>(c, s, sm.bnd[c], sm.bnd[c + 1], sm.anc[c], ev, sm, Ls, Lc, gbl,
+                                     r_out);
+    }
     if (LEARN) {
       if (BM == 0) {
         float acc = 0.f;
@@ -428,27 +666,79 @@ __device__ double evaluate(int NC, TP t, UP u, WP w, float T, int Mrt, Sm<M> &sm
     }
   }
   // Part2 and Part3 terms for this thread's share of the parameters
-  double part = ((double)Ls - (double)Lc) * kLn2;
+  float Ps = 0.f, Pc = 0.f;
   for (int p = tid; p < Mrt + Mrt * Mrt; p += blockDim.x) {
     if (p < Mrt) {
-      part -= (double)T * (double)sm.mu[p];
+      kahan_add(Ps, Pc, -T * sm.mu[p]);
     } else {
       const int q = p - Mrt, i = q / Mrt, j = q % Mrt;
-      part -= (double)sm.alpha[i * AP + j] * (double)sm.C[j];
+      kahan_add(Ps, Pc, -sm.alpha[i * AP + j] * sm.C[j]);
     }
   }
-  return block_sum_double(part, sm.red);  // contains the barrier after the atomics
+  float h1 = Ls, l1 = -Lc, h2 = Ps, l2 = -Pc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float a = __shfl_xor_sync(0xffffffffu, h1, o), b = __shfl_xor_sync(0xffffffffu, l1, o);
+    const float cc = __shfl_xor_sync(0xffffffffu, h2, o), d = __shfl_xor_sync(0xffffffffu, l2, o);
+    pair_add(h1, l1, a);
+    l1 += b;
+    pair_add(h2, l2, cc);
+    l2 += d;
+  }
+  if ((tid & 31) == 0) reinterpret_cast<float4 *>(sm.red)[tid >> 5] = make_float4(h1, l1, h2, l2);
+  __syncthreads();
+}
+
+// lnL from the per-warp partials (FP64: the only double arithmetic per evaluation).
+template <int M>
+__device__ __forceinline__ double lnl_total(const Sm<M> &sm) {
+  const int nw = (blockDim.x + 31) >> 5;
+  const float4 *r4 = reinterpret_cast<const float4 *>(sm.red);
+  double p1 = 0.0, p23 = 0.0;
+  for (int w = 0; w < nw; ++w) {
+    const float4 v = r4[w];
+    p1 += (double)v.x + (double)v.y;
+    p23 += (double)v.z + (double)v.w;
+  }
+  return p1 * kLn2 + p23;
+}
+
+// Event sum of d/dalpha_ij (over the private slots, or the shared copy).
+template <int M, int SPL>
+__device__ __forceinline__ float alpha_event_sum(int i, int j, const Sm<M> &sm) {
+  if (UsePriv<M>::value) {
+    constexpr int MS = M / SPL;
+    constexpr int NQ = MS / 4;
+    const int NT = blockDim.x, NC = NT / SPL;
+    const int s = j / MS, jj = j % MS, q = jj / 4, e = jj % 4;
+    const float *base = sm.gpriv + ((i * NQ + q) * NT) * 4 + e;
+    float acc = 0.f;
+    for (int c = 0; c < NC; ++c) acc += base[(c * SPL + s) * 4];
+    return acc;
+  }
+  return sm.ga[i * (M + 1) + j];
+}
+
+template <int M, int SPL>
+__device__ __forceinline__ float mu_event_sum(int i, const Sm<M> &sm) {
+  if (UsePriv<M>::value) {
+    const int NC = blockDim.x / SPL;
+    float acc = 0.f;
+    for (int c = 0; c < NC; ++c) acc += sm.mpriv[i * NC + c];
+    return acc;
+  }
+  return sm.gm[i];
 }
 
 // Final gradient of parameter p (compact index: mu | alpha | beta).
-template <int M, int BM, bool LEARN>
+template <int M, int SPL, int BM, bool LEARN>
 __device__ __forceinline__ float grad_of(int p, int Mrt, float T, const Sm<M> &sm) {
-  constexpr int AP = M + 1;
-  if (p < Mrt) return sm.gm[p] - T;
+  constexpr int AP = M + 4;
+  if (p < Mrt) return mu_event_sum<M, SPL>(p, sm) - T;
   const int q = p - Mrt;
   if (q < Mrt * Mrt) {
     const int i = q / Mrt, j = q % Mrt;
-    return sm.ga[i * AP + j] - sm.C[j];
+    return alpha_event_sum<M, SPL>(i, j, sm) - sm.C[j];
   }
   if (!LEARN) return 0.f;
   const int jb = q - Mrt * Mrt;
@@ -468,21 +758,11 @@ __device__ __forceinline__ float grad_of(int p, int Mrt, float T, const Sm<M> &s
 
 template <int M>
 __device__ __forceinline__ float &param_ref(int p, int Mrt, Sm<M> &sm) {
-  constexpr int AP = M + 1;
+  constexpr int AP = M + 4;
   if (p < Mrt) return sm.mu[p];
   const int q = p - Mrt;
   if (q < Mrt * Mrt) return sm.alpha[(q / Mrt) * AP + (q % Mrt)];
   return sm.beta[q - Mrt * Mrt];
-}
-
-template <int M>
-__device__ __forceinline__ void zero_accumulators(Sm<M> &sm) {
-  constexpr int AP = M + 1;
-  for (int p = threadIdx.x; p < M * AP; p += blockDim.x) sm.ga[p] = 0.f;
-  for (int j = threadIdx.x; j < M; j += blockDim.x) {
-    sm.gm[j] = 0.f;
-    sm.gb[j] = 0.f;
-  }
 }
 
 }  // namespace mdhp
