@@ -188,12 +188,25 @@ mdhp_status mdhp_fit_batch(mdhp_plan *plan, const mdhp_batch *batch, const mdhp_
 mdhp_status mdhp_plan_set_timing(mdhp_plan *plan, int32_t enable);
 float mdhp_plan_last_fit_ms(mdhp_plan *plan);
 
-/* Launch shape chosen for a length class (for tests and reports):
- * threads per window, threads per chunk, and the shared-memory cutoff. */
+/* Launch shape (for tests, reports and tuning): threads per window and
+ * threads per chunk of the event recursion, and the shared-memory cutoff:
+ * windows of at most this many events are staged in shared memory (the
+ * recursion) or keep their decoupled features in shared memory (fixed beta);
+ * longer windows stream from device memory.  A cutoff of 0 streams all. */
 mdhp_status mdhp_plan_get_shape(const mdhp_plan *plan, int32_t *threads_per_window,
                                 int32_t *threads_per_chunk, int32_t *smem_cutoff_events);
 mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
                                 int32_t threads_per_chunk, int32_t smem_cutoff_events);
+
+/* Kernel family used by mdhp_fit_batch for fixed beta:
+ *   MDHP_PATH_AUTO (0)      decoupled features when the plan has scratch for
+ *                           them (M <= 32 and a stated max_events_per_window),
+ *                           else the event recursion;
+ *   MDHP_PATH_RECURSION (1) always re-run the event recursion each iteration.
+ * Both compute the same quantities; the choice only affects speed. */
+#define MDHP_PATH_AUTO 0
+#define MDHP_PATH_RECURSION 1
+mdhp_status mdhp_plan_set_path(mdhp_plan *plan, int32_t path);
 
 /* Text of the last error in this thread (static storage). */
 const char *mdhp_last_error(void);

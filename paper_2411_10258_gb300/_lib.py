@@ -46,6 +46,7 @@ SIGNATURES = [
     ("mdhp_plan_last_fit_ms", ctypes.c_float, [P]),
     ("mdhp_plan_get_shape", ctypes.c_int, [P, P, P, P]),
     ("mdhp_plan_set_shape", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    ("mdhp_plan_set_path", ctypes.c_int, [P, ctypes.c_int32]),
     ("mdhp_last_error", ctypes.c_char_p, []),
     ("mdhp_version", ctypes.c_int32, []),
 ]

@@ -154,6 +154,11 @@ class Plan:
         _lib.check(self.lib.mdhp_plan_get_shape(self.h, *[ctypes.byref(x) for x in v]), "get_shape")
         return tuple(x.value for x in v)
 
+    def set_path(self, path: str):
+        """'auto' (decoupled features for fixed beta when possible) or 'recursion'."""
+        code = {"auto": 0, "recursion": 1}[path]
+        _lib.check(self.lib.mdhp_plan_set_path(self.h, code), "mdhp_plan_set_path")
+
     def set_shape(self, threads_per_window: int, threads_per_chunk: int, cutoff: int):
         _lib.check(self.lib.mdhp_plan_set_shape(self.h, threads_per_window, threads_per_chunk, cutoff),
                    "mdhp_plan_set_shape")

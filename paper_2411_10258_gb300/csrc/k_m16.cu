@@ -17,4 +17,9 @@ FitFn get_fit_m16(int SPL, int BM, bool learn, bool stage) {
 
 WgFn get_wg_m16(int BM) { return BM == 0 ? k_weight_grad<16, 0> : k_weight_grad<16, 1>; }
 
+FitFn get_fitx_m16(int BM, bool xs) {
+  if (BM == 0) return xs ? k_fit_x<16, 0, true> : k_fit_x<16, 0, false>;
+  return xs ? k_fit_x<16, 1, true> : k_fit_x<16, 1, false>;
+}
+
 }  // namespace mdhp

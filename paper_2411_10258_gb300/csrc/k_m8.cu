@@ -15,4 +15,9 @@ FitFn get_fit_m8(int SPL, int BM, bool learn, bool stage) {
 
 WgFn get_wg_m8(int BM) { return BM == 0 ? k_weight_grad<8, 0> : k_weight_grad<8, 1>; }
 
+FitFn get_fitx_m8(int BM, bool xs) {
+  if (BM == 0) return xs ? k_fit_x<8, 0, true> : k_fit_x<8, 0, false>;
+  return xs ? k_fit_x<8, 1, true> : k_fit_x<8, 1, false>;
+}
+
 }  // namespace mdhp

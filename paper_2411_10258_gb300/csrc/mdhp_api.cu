@@ -59,6 +59,16 @@ FitFn get_fit(int M, int SPL, int BM, bool learn, bool stage) {
   }
   return nullptr;
 }
+FitFn get_fitx(int M, int BM, bool xs) {
+  switch (M) {
+    case 4: return get_fitx_m4(BM, xs);
+    case 8: return get_fitx_m8(BM, xs);
+    case 16: return get_fitx_m16(BM, xs);
+    case 32: return get_fitx_m32(BM, xs);
+    case 64: return get_fitx_m64(BM, xs);
+  }
+  return nullptr;
+}
 WgFn get_wg(int M, int BM) {
   switch (M) {
     case 4: return get_wg_m4(BM);
@@ -147,6 +157,12 @@ struct mdhp_plan {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
   int timing = 0, timed = 0;
+  // decoupled fixed-beta fit: per-CTA feature scratch for windows of up to xcap events
+  float4 *xbuf = nullptr;
+  int xcap = 0, xgrid = 0, xnt = 128;
+  int xres = 0, xrgrid = 0;  // windows of <= xres events keep their features in shared memory
+  int xres_max = 0;          // largest shared-memory class the device allows
+  int use_x = 1;  // 0 forces the recursion kernels (for tests and comparisons)
 };
 
 extern "C" {
@@ -283,6 +299,44 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
                                               p->idx, p->order, max_windows);
     ok &= cudaMalloc(&p->sort_tmp, p->sort_tmp_bytes > 0 ? p->sort_tmp_bytes : 16) == cudaSuccess;
   }
+  if (ok && p->Mt <= 32 && max_events_per_window > 0 && max_events_per_window < (1 << 26)) {
+    FitFn fx = get_fitx(p->Mt, beta_mode, false);
+    const Carve cx = make_carve_x(p->Mt, p->xnt, 0, true);
+    int occ = 0;
+    if (fx && prepare_kernel((const void *)fx, cx.total) == MDHP_OK &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fx, p->xnt, cx.total) == cudaSuccess &&
+        occ > 0) {
+      p->xgrid = num_sms() * occ;
+      p->xcap = (int)max_events_per_window;
+      const size_t bytes = (size_t)p->xgrid * (size_t)(p->Mt / 4) * (size_t)p->xcap * sizeof(float4);
+      if (cudaMalloc(&p->xbuf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p->xbuf = nullptr;  // the recursion kernels still work without it
+        p->xcap = 0;
+      }
+    }
+    // shared-memory class: two CTAs per SM for M <= 16, one for M = 32
+    FitFn fr = get_fitx(p->Mt, beta_mode, true);
+    const int fixed = make_carve_x(p->Mt, p->xnt, 0, true).total;
+    const int target = (p->Mt <= 16 ? max_dyn_smem() / 2 : max_dyn_smem()) - 1024;
+    int cap = (target - fixed) / (p->Mt * 4);
+    cap = cap / 32 * 32;
+    if (p->xbuf && fr && cap >= 64) {
+      if (cap > p->xcap) cap = p->xcap;
+      const Carve cr = make_carve_x(p->Mt, p->xnt, cap, true);
+      int occr = 0;
+      if (prepare_kernel((const void *)fr, cr.total) == MDHP_OK &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occr, fr, p->xnt, cr.total) == cudaSuccess &&
+          occr > 0) {
+        p->xres_max = cap;
+        p->xrgrid = num_sms() * occr;
+        // measured default: for M <= 16 the shared-memory class takes the L1
+        // capacity the global-feature class relies on, so it is off
+        p->xres = p->Mt >= 32 ? cap : 0;
+      }
+    }
+    cudaGetLastError();
+  }
   ok &= cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) == cudaSuccess;
   ok &= cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   ok &= cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) == cudaSuccess;
@@ -305,6 +359,7 @@ void mdhp_plan_destroy(mdhp_plan *p) {
   cudaFree(p->order);
   cudaFree(p->ctl);
   cudaFree(p->sort_tmp);
+  cudaFree(p->xbuf);
   if (p->side) cudaStreamDestroy(p->side);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
@@ -328,11 +383,18 @@ float mdhp_plan_last_fit_ms(mdhp_plan *p) {
   return ms;
 }
 
+mdhp_status mdhp_plan_set_path(mdhp_plan *p, int32_t path) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  if (path != MDHP_PATH_AUTO && path != MDHP_PATH_RECURSION) return fail(MDHP_E_ARG, "path %d", path);
+  p->use_x = path == MDHP_PATH_AUTO ? 1 : 0;
+  return MDHP_OK;
+}
+
 mdhp_status mdhp_plan_get_shape(const mdhp_plan *p, int32_t *nt, int32_t *spl, int32_t *cutoff) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
   if (nt) *nt = p->shape.nt;
   if (spl) *spl = p->shape.spl;
-  if (cutoff) *cutoff = p->shape.cutoff;
+  if (cutoff) *cutoff = p->use_x && p->xbuf ? p->xres : p->shape.cutoff;
   return MDHP_OK;
 }
 
@@ -344,6 +406,8 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *p, int32_t nt, int32_t spl, int32_t c
     return fail(MDHP_E_UNSUPPORTED, "threads per chunk %d not built for M<=%d", spl, p->Mt);
   if (cutoff < 0) return fail(MDHP_E_ARG, "cutoff < 0");
   p->shape = Shape{nt, spl, cutoff};
+  p->xres = cutoff < p->xres_max ? (cutoff / 32) * 32 : p->xres_max;
+  if (p->xres < 64) p->xres = 0;
   return MDHP_OK;
 }
 
@@ -382,7 +446,11 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   if (cub::DeviceRadixSort::SortPairsDescending(p->sort_tmp, tmp, p->keys, p->keys_sorted, p->idx,
                                                 p->order, B, 0, 32, st) != cudaSuccess)
     return cuda_check("radix sort");
-  k_split<<<1, 32, 0, st>>>(p->keys_sorted, B, ev_cap, need_long ? 1 : 0, p->ctl);
+  const bool xpath = p->use_x && !learn && p->xbuf && bound > 0 && bound <= p->xcap;
+  // decoupled path: windows longer than the shared-memory class form the first range
+  const int xcut = p->xres > 0 ? p->xres : -1;
+  k_split<<<1, 32, 0, st>>>(p->keys_sorted, B, xpath ? xcut : ev_cap, (xpath || need_long) ? 1 : 0,
+                            p->ctl);
   if ((s = cuda_check("k_split")) != MDHP_OK) return s;
 
   FitArgs a{};
@@ -395,6 +463,52 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   a.alpha_floor = o->alpha_floor; a.beta_floor = o->beta_floor; a.b1 = o->adam_b1;
   a.b2 = o->adam_b2; a.eps = o->adam_eps; a.tol = o->tol;
 
+  if (xpath) {
+    // long windows: features in the per-CTA global scratch (side stream);
+    // short windows: features in shared memory (this stream); both queues
+    // are taken longest first
+    FitArgs ax = a;
+    ax.xbuf = p->xbuf;
+    const bool any_long = !(p->xres > 0 && bound <= p->xres);
+    if (p->timing) cudaEventRecord(p->ev_t0, st);
+    if (any_long) {
+      FitFn fx = get_fitx(p->Mt, p->beta_mode, false);
+      FitArgs al = ax;
+      al.queue = p->ctl + 0;
+      al.range = p->ctl + 2;
+      al.ev_cap = p->xcap;
+      al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1);
+      if ((s = prepare_kernel((const void *)fx, al.carve.total)) != MDHP_OK) return s;
+      cudaStream_t ls = st;
+      if (p->xres > 0) {
+        cudaEventRecord(p->ev_fork, st);
+        cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+        ls = p->side;
+      }
+      fx<<<p->xgrid, p->xnt, al.carve.total, ls>>>(al);
+      if ((s = cuda_check("k_fit_x (global features)")) != MDHP_OK) return s;
+      if (p->xres > 0) cudaEventRecord(p->ev_join, p->side);
+    }
+    if (p->xres > 0) {
+      FitFn fr = get_fitx(p->Mt, p->beta_mode, true);
+      FitArgs ar = ax;
+      ar.queue = p->ctl + 1;
+      ar.range = p->ctl + 4;
+      ar.ev_cap = p->xres;
+      ar.carve = make_carve_x(p->Mt, p->xnt, p->xres, o->optimizer == 1);
+      if ((s = prepare_kernel((const void *)fr, ar.carve.total)) != MDHP_OK) return s;
+      int grid = p->xrgrid;
+      if (grid > B) grid = B;
+      fr<<<grid, p->xnt, ar.carve.total, st>>>(ar);
+      if ((s = cuda_check("k_fit_x (shared features)")) != MDHP_OK) return s;
+      if (any_long) cudaStreamWaitEvent(st, p->ev_join, 0);
+    }
+    if (p->timing) {
+      cudaEventRecord(p->ev_t1, st);
+      p->timed = 1;
+    }
+    return MDHP_OK;
+  }
   if (p->timing) cudaEventRecord(p->ev_t0, st);
   if (need_long) {
     FitFn fl = get_fit(p->Mt, sh.spl, p->beta_mode, learn, false);

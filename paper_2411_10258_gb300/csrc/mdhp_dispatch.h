@@ -4,6 +4,7 @@
 #pragma once
 
 #include "mdhp_kernels.cuh"
+#include "mdhp_fitx.cuh"
 
 namespace mdhp {
 
@@ -15,11 +16,13 @@ using WgFn = void (*)(WgArgs);
 LlgFn get_llg(int M, int SPL, int BM, bool learn, bool stage);
 FitFn get_fit(int M, int SPL, int BM, bool learn, bool stage);
 WgFn get_wg(int M, int BM);
+FitFn get_fitx(int M, int BM, bool xs);
 
 #define MDHP_DECLARE_M(MV)                                                   \
   LlgFn get_llg_m##MV(int SPL, int BM, bool learn, bool stage);              \
   FitFn get_fit_m##MV(int SPL, int BM, bool learn, bool stage);              \
-  WgFn get_wg_m##MV(int BM);
+  WgFn get_wg_m##MV(int BM);                                                 \
+  FitFn get_fitx_m##MV(int BM, bool xs);
 MDHP_DECLARE_M(4)
 MDHP_DECLARE_M(8)
 MDHP_DECLARE_M(16)

@@ -1,0 +1,353 @@
+// Decoupled fixed-beta fit.
+//
+// With beta fixed, every state R_j(t_n) = sum_{k in j, t_k < t_n} w_k
+// exp(-beta_j (t_n - t_k)) is independent of the parameters being fitted
+// (mu, alpha): the paper's "decoupling" of Stage 1 (Sec. IV-B.3), which
+// hoists everything parameter-free out of the descent loop.  This kernel
+// computes the features x_n = R(t_n) once per window by the chunked recursion
+// (pass 1 + scan + one feature walk), stores them grouped by event type
+// (a stable counting sort: type-major, time order within a type), and then
+// runs every iteration as a dense pass over the features:
+//   lambda_n = mu_i + alpha_i . x_n,  r_n = 1 / lambda_n,
+//   d/dalpha_i += r_n x_n,  d/dmu_i += r_n,  Part1 += ln lambda_n  (i = type of n)
+// Each thread owns a contiguous range of the sorted features, so the row
+// alpha_i and the sums d/dalpha_i stay in registers with static indices; a
+// thread's partial sums of type i go to segment slot (thread + i), which is
+// unique (ranges and types are both ordered), and the slots of a type are
+// contiguous, so the block reduction needs no atomics.  Features live in
+// shared memory (XS) or in a per-CTA global scratch slot read through L1/L2.
+// Part2 + Part3 use the compensator constants of the state at T_span.
+#pragma once
+
+#include "mdhp_solver.cuh"
+
+namespace mdhp {
+
+// Feature layout: in shared memory, slices as planes [q][pos] (a warp's lanes
+// read positions an odd stride apart: distinct bank groups); in global memory,
+// rows [pos][q] (a lane's features are contiguous, so its L1 lines are reused
+// by its next position).
+template <bool XS>
+__device__ __forceinline__ int xidx(int q, int pos, int xcap, int NQ) {
+  return XS ? q * xcap + pos : pos * NQ + q;
+}
+
+// Counting sort of the window's events by type and the feature walk.
+// Needs bnd/anc (NT chunks), encR (entering states), cnt (events per type).
+// Writes X[q * xcap + pos] (float4 slices of x_n) and tstart[0..M].
+template <int M, int BM, bool XS, typename EV, typename XP>
+__device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, int xcap) {
+  constexpr int AP = M + 4;
+  constexpr int NQ = M / 4;
+  const int tid = threadIdx.x, NT = blockDim.x, NC = NT;
+  int *ctr = reinterpret_cast<int *>(sm.P);  // [type][chunk]
+  for (int p = tid; p < M * NC; p += NT) ctr[p] = 0;
+  if (tid == 0) {
+    int acc = 0;
+    for (int i = 0; i < M; ++i) {
+      sm.tstart[i] = acc;
+      acc += (i < Mrt) ? sm.cnt[i] : 0;
+    }
+    sm.tstart[M] = acc;
+  }
+  __syncthreads();
+  const int c = tid;
+  const int b0 = sm.bnd[c], b1 = sm.bnd[c + 1];
+  for (int n = b0; n < b1; ++n) ctr[ev.id(n) * NC + c] += 1;
+  __syncthreads();
+  if (tid < M) {  // exclusive scan over chunks, per type, from the type's start
+    int run = sm.tstart[tid];
+    for (int cc = 0; cc < NC; ++cc) {
+      const int v = ctr[tid * NC + cc];
+      ctr[tid * NC + cc] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  // walk the chunk in time order from its entering state; x_n = state at t_n
+  Walker<M, BM, false> wk;
+  wk.load_beta(sm.bl2, 0);
+#pragma unroll
+  for (int j = 0; j < M; ++j) wk.R[j] = sm.encR[c * M + j];
+  float tprev = sm.anc[c];
+  int gs = b0;
+  for (int n = b0; n < b1; ++n) {
+    float tn;
+    int un;
+    ev.get(n, tn, un);
+    if (tn > tprev) {
+      for (int k = gs; k < n; ++k) wk.add(sm.oh + ev.id(k) * AP, ev.wt(k));
+      wk.decay(tn - tprev);
+      tprev = tn;
+      gs = n;
+    }
+    const int pos = ctr[un * NC + c];
+    ctr[un * NC + c] = pos + 1;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      X[xidx<XS>(q, pos, xcap, NQ)] =
+          make_float4(wk.R[4 * q], wk.R[4 * q + 1], wk.R[4 * q + 2], wk.R[4 * q + 3]);
+  }
+  __syncthreads();
+}
+
+// One evaluation over the sorted features: this thread's range [p0, p1),
+// starting in type i0.  Segment sums go to P[(tid + i) * (M + 4) + 0..M].
+template <int M, bool XS, typename XP>
+__device__ __forceinline__ void xpass(int p0, int p1, int i0, XP X, int xcap, const Sm<M> &sm,
+                                      float &Ls, float &Lc) {
+  constexpr int NQ = M / 4;
+  constexpr int AP = M + 4;
+  constexpr int PP = M + 4;
+  if (p0 >= p1) return;
+  const int tid = threadIdx.x;
+  int i = i0;
+  int te = sm.tstart[i + 1];
+  float4 ar[NQ];
+  float mu = sm.mu[i];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) ar[q] = reinterpret_cast<const float4 *>(sm.alpha + i * AP)[q];
+  float4 g[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) g[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  float gm = 0.f;
+  float4 xn[NQ];  // next position's features, loaded one step ahead
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) xn[q] = X[xidx<XS>(q, p0, xcap, NQ)];
+  for (int p = p0; p < p1; ++p) {
+    float4 x[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) x[q] = xn[q];
+    if (p + 1 < p1) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) xn[q] = X[xidx<XS>(q, p + 1, xcap, NQ)];
+    }
+    while (p >= te) {  // leave type i (types with no events are passed over)
+      float4 *slot = reinterpret_cast<float4 *>(sm.P + (tid + i) * PP);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        slot[q] = g[q];
+        g[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      sm.P[(tid + i) * PP + M] = gm;
+      gm = 0.f;
+      ++i;
+      te = sm.tstart[i + 1];
+      mu = sm.mu[i];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) ar[q] = reinterpret_cast<const float4 *>(sm.alpha + i * AP)[q];
+    }
+    float d0 = mu, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      d0 = fmaf(ar[q].x, x[q].x, d0);
+      d1 = fmaf(ar[q].y, x[q].y, d1);
+      d2 = fmaf(ar[q].z, x[q].z, d2);
+      d3 = fmaf(ar[q].w, x[q].w, d3);
+    }
+    const float lam = (d0 + d1) + (d2 + d3);
+    const float r = __fdividef(1.f, lam);
+    kahan_add(Ls, Lc, __log2f(lam));
+    gm += r;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      g[q].x = fmaf(r, x[q].x, g[q].x);
+      g[q].y = fmaf(r, x[q].y, g[q].y);
+      g[q].z = fmaf(r, x[q].z, g[q].z);
+      g[q].w = fmaf(r, x[q].w, g[q].w);
+    }
+  }
+  float4 *slot = reinterpret_cast<float4 *>(sm.P + (tid + i) * PP);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) slot[q] = g[q];
+  sm.P[(tid + i) * PP + M] = gm;
+}
+
+// Event part of the gradient of parameter p (mu_i or alpha_ij): the sum of
+// the segment slots of type i.
+template <int M>
+__device__ __forceinline__ float xseg_sum(int i, int j, const Sm<M> &sm) {
+  constexpr int PP = M + 4;
+  if (sm.tstart[i + 1] <= sm.tstart[i]) return 0.f;
+  float acc = 0.f;
+  for (int t = sm.tf[i]; t <= sm.tl[i]; ++t) acc += sm.P[(t + i) * PP + j];
+  return acc;
+}
+
+template <int M, int BM, bool XS>
+__global__ void __launch_bounds__(128, (M >= 32 ? 3 : 4)) k_fit_x(FitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Sm<M> sm;
+  sm.bind(smem, a.carve);
+  constexpr int AP = M + 4;
+  const int Mrt = a.Mrt;
+  const int nb = BM == 0 ? 1 : Mrt;
+  const int np = Mrt + Mrt * Mrt + nb;
+  const int nupd = Mrt + Mrt * Mrt;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int xcap = a.ev_cap;
+  float4 *Xg = XS ? nullptr : a.xbuf + (size_t)blockIdx.x * (M / 4) * (size_t)xcap;
+  for (;;) {
+    if (tid == 0) sm.ctl[1] = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int q = sm.ctl[1];
+    const int qb = a.range ? a.range[0] : a.qbegin;
+    const int qe = a.range ? a.range[1] : a.qend;
+    __syncthreads();
+    if (qb + q >= qe) break;
+    const int b = a.order ? a.order[qb + q] : qb + q;
+    const int64_t o0 = a.offsets[b];
+    const int N = (int)(a.offsets[b + 1] - o0);
+    const float T = a.T[b];
+    const float *tg = a.t + o0;
+    const int16_t *ug = a.id + o0;
+    const float *wg = a.w ? a.w + o0 : nullptr;
+    int st = (N > xcap) ? (int)kE_ARG : stage_and_validate<M, false>(tg, ug, wg, N, T, Mrt, sm);
+    if (st != kOK) {
+      if (tid == 0) {
+        a.status[b] = st;
+        a.loglik[b] = __longlong_as_double(0x7ff8000000000000LL);
+        a.iters[b] = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    load_params<M, BM>(b, Mrt, a.mu, a.alpha, a.beta, sm);
+    __syncthreads();
+    if (a.init == 1) {
+      for (int p = tid; p < Mrt * Mrt; p += NT) {
+        const int i = p / Mrt, j = p % Mrt;
+        sm.alpha[i * AP + j] = 0.5f * sm.beta[BM == 0 ? 0 : j] / (float)Mrt;
+      }
+      for (int i = tid; i < Mrt; i += NT) sm.mu[i] = 0.5f * (float)max(sm.cnt[i], 1) / T;
+    }
+    if (a.optimizer == 1) {
+      for (int p = tid; p < np; p += NT) {
+        sm.am[p] = 0.f;
+        sm.av[p] = 0.f;
+      }
+    }
+    const EvG ev{tg, ug, wg};
+    setup_chunks(NT, N, T, ev, sm.bnd, sm.anc);
+    prepare_states<M, 1, BM, false>(NT, ev, Mrt, sm);
+    if (XS) build_features<M, BM, true>(N, ev, Mrt, sm, sm.xs, xcap);
+    else build_features<M, BM, false>(N, ev, Mrt, sm, Xg, xcap);
+    // thread ranges over the sorted features; an odd length keeps the
+    // lanes' float4 reads on distinct bank groups
+    int L = (N + NT - 1) / NT;
+    L = max(L | 1, 1);
+    const int p0 = min(tid * L, N), p1 = min(p0 + L, N);
+    int i0 = 0;
+    while (i0 < M - 1 && sm.tstart[i0 + 1] <= p0) ++i0;
+    for (int i = tid; i < M; i += NT) {
+      sm.tf[i] = sm.tstart[i] / L;
+      sm.tl[i] = sm.tstart[i + 1] > sm.tstart[i] ? (sm.tstart[i + 1] - 1) / L : -1;
+    }
+    __syncthreads();
+    const float invN = 1.f / (float)max(N, 1);
+    double lnl_prev = 0.0, lnl_out = 0.0;
+    int streak = 0, k = 0;
+    int wst = a.tol > 0.0 ? kE_MAXITER : kOK;
+    float b1t = 1.f, b2t = 1.f;
+    for (k = 0; k < a.max_iters; ++k) {
+      float Ls = 0.f, Lc = 0.f;
+      if (XS) xpass<M, true>(p0, p1, i0, (const float4 *)sm.xs, xcap, sm, Ls, Lc);
+      else xpass<M, false>(p0, p1, i0, (const float4 *)Xg, xcap, sm, Ls, Lc);
+      // Part2 + Part3 and the block sums (ends with a barrier)
+      float Ps = 0.f, Pc = 0.f;
+      for (int p = tid; p < M + M * M; p += NT) {  // padded entries hold zeros
+        if (p < M) {
+          kahan_add(Ps, Pc, -T * sm.mu[p]);
+        } else {
+          const int qq = p - M, i = qq / M, j = qq % M;
+          kahan_add(Ps, Pc, -sm.alpha[i * AP + j] * sm.C[j]);
+        }
+      }
+      float h1 = Ls, l1 = -Lc, h2 = Ps, l2 = -Pc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float x1 = __shfl_xor_sync(0xffffffffu, h1, o), y1 = __shfl_xor_sync(0xffffffffu, l1, o);
+        const float x2 = __shfl_xor_sync(0xffffffffu, h2, o), y2 = __shfl_xor_sync(0xffffffffu, l2, o);
+        pair_add(h1, l1, x1);
+        l1 += y1;
+        pair_add(h2, l2, x2);
+        l2 += y2;
+      }
+      if ((tid & 31) == 0) reinterpret_cast<float4 *>(sm.red)[tid >> 5] = make_float4(h1, l1, h2, l2);
+      __syncthreads();
+      int bad = 0;
+      if (tid == 0) {
+        const double val = lnl_total(sm);
+        bad = !isfinite(val);
+        int decision = 0;
+        if (!bad) {
+          if (k > 0 && a.tol > 0.0 && fabs(val - lnl_prev) <= a.tol * fabs(val)) ++streak;
+          else streak = 0;
+          lnl_prev = val;
+          lnl_out = val;
+          if (a.tol > 0.0 && streak >= a.patience) { wst = kOK; decision = 1; }
+          else if (k == a.max_iters - 1) decision = 1;
+        } else if (k == 0) {
+          lnl_out = val;
+        }
+        sm.ctl[2] = decision;
+      }
+      // gradient and tentative update of this thread's parameters (each
+      // parameter always belongs to the same thread): gbuf keeps theta_k and
+      // prev theta_{k-1}, so a stop returns theta_k and a non-finite
+      // evaluation returns the last finite point theta_{k-1}
+      b1t *= a.b1;
+      b2t *= a.b2;
+      for (int p = tid; p < M + M * M; p += NT) {
+        int i, j, pc;
+        if (p < M) {
+          i = p; j = M; pc = p;
+        } else {
+          i = (p - M) / M; j = (p - M) % M; pc = Mrt + i * Mrt + j;
+        }
+        if (i >= Mrt || (j < M && j >= Mrt)) continue;
+        const float g = xseg_sum<M>(i, j, sm) - (j == M ? T : sm.C[j]);
+        bad |= !isfinite(g);
+        float &th = (j == M) ? sm.mu[i] : sm.alpha[i * AP + j];
+        const float gs = g * invN;
+        float step;
+        if (a.optimizer == 1) {
+          const float m1 = a.b1 * sm.am[pc] + (1.f - a.b1) * gs;
+          const float m2 = a.b2 * sm.av[pc] + (1.f - a.b2) * gs * gs;
+          sm.am[pc] = m1;
+          sm.av[pc] = m2;
+          const float mh = m1 / (1.f - b1t), vh = m2 / (1.f - b2t);
+          step = a.lr * mh / (sqrtf(vh) + a.eps);
+        } else {
+          step = a.lr * gs;
+        }
+        const float fl = (j == M) ? a.mu_floor : a.alpha_floor;
+        sm.prev[pc] = sm.gbuf[pc];
+        sm.gbuf[pc] = th;
+        th = fmaxf(th + step, fl);
+      }
+      bad = __syncthreads_or(bad);
+      const int stop = bad ? 1 : sm.ctl[2];
+      if (stop) {
+        const float *src = (bad && k > 0) ? sm.prev : sm.gbuf;
+        for (int p = tid; p < nupd; p += NT) param_ref<M>(p, Mrt, sm) = src[p];
+        if (bad) wst = kE_NONFINITE;
+        else ++k;
+        __syncthreads();
+        break;
+      }
+    }
+    for (int p = tid; p < Mrt * Mrt; p += NT)
+      a.alpha[(int64_t)b * Mrt * Mrt + p] = sm.alpha[(p / Mrt) * AP + (p % Mrt)];
+    for (int i = tid; i < Mrt; i += NT) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];
+    for (int j = tid; j < nb; j += NT) a.beta[(int64_t)b * nb + j] = sm.beta[j];
+    if (tid == 0) {
+      a.loglik[b] = lnl_out;
+      a.iters[b] = k;
+      a.status[b] = wst;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace mdhp

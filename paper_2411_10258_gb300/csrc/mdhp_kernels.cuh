@@ -39,6 +39,7 @@ struct FitArgs {
   int optimizer, max_iters, fit_beta, patience, init;
   float lr, mu_floor, alpha_floor, beta_floor, b1, b2, eps;
   double tol;
+  float4 *xbuf;  // decoupled fit: per-CTA feature scratch (global), or nullptr
   Carve carve;
 };
 

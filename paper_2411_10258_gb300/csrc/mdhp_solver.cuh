@@ -129,7 +129,7 @@ __device__ __forceinline__ int chunk_begin(int c, int NC, int N, const EV &ev) {
 struct Carve {
   // byte offsets
   int alpha, oh, ga, mu, gm, beta, bl2, gb, W, cnt, C, dC, endR, endS, anc, bnd, encR, encS, prev,
-      gbuf, am, av, red, ctl, gpriv, mpriv, ev_t, ev_u, ev_w;
+      gbuf, am, av, red, ctl, gpriv, mpriv, ev_t, ev_u, ev_w, tstart, tf, tl, P, xs;
   int total;
 };
 
@@ -139,7 +139,7 @@ __host__ __device__ inline int pitch4(int M) { return M + 4; }  // 16-byte rows,
 __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, bool weights,
                                             bool learn, bool adam, bool fit, bool priv) {
   const int NC = NT / SPL;
-  Carve c;
+  Carve c = {};
   int o = 0;
   const int AP = pitch4(M);
   const int npm = M + M * M + M;
@@ -177,12 +177,57 @@ __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, 
   return c;
 }
 
+// Carve of the decoupled fixed-beta fit (features x_n = R(t_n) stored once per
+// window, grouped by event type).  NT threads = NT chunks; P holds the
+// per-thread segment sums, (NT + M) slots of M + 4 floats (the chunk/type
+// counters of the feature pass share the same space); xcap > 0 places the
+// features in shared memory (xcap events x M floats).
+__host__ __device__ inline Carve make_carve_x(int M, int NT, int xcap, bool adam) {
+  Carve c = {};
+  int o = 0;
+  const int AP = pitch4(M);
+  const int npm = M + M * M + M;
+  auto take = [&](int bytes) { int r = o; o = align_up(o + bytes, 16); return r; };
+  c.red = take(32 * 8);
+  c.ctl = take(16 * 4);
+  c.alpha = take(M * AP * 4);
+  c.oh = take(M * AP * 4);
+  c.mu = take(M * 4);
+  c.gm = take(M * 4);
+  c.beta = take(M * 4);
+  c.bl2 = take(M * 4);
+  c.gb = take(M * 4);
+  c.W = take(M * 8);
+  c.cnt = take(M * 4);
+  c.C = take(M * 4);
+  c.dC = take(M * 4);
+  c.endR = take(M * 4);
+  c.endS = take(M * 4);
+  c.anc = take((NT + 1) * 4);
+  c.bnd = take((NT + 1) * 4);
+  c.encR = take(NT * M * 4);
+  c.encS = c.encR;
+  c.prev = take(npm * 4);
+  c.gbuf = take(npm * 4);
+  c.am = adam ? take(npm * 4) : 0;
+  c.av = adam ? take(npm * 4) : 0;
+  c.tstart = take((M + 1) * 4);
+  c.tf = take(M * 4);
+  c.tl = take(M * 4);
+  c.P = take((NT + M) * (M + 4) * 4);
+  c.xs = xcap > 0 ? take(xcap * M * 4) : 0;
+  c.total = o;
+  return c;
+}
+
 template <int M>
 struct Sm {
   double *W;  // per-type weight sums (exact for counts, FP64 for weights)
   float *alpha, *oh, *ga, *mu, *gm, *beta, *bl2, *gb, *C, *dC, *endR, *endS, *anc, *encR,
       *encS, *prev, *gbuf, *am, *av, *gpriv, *mpriv;
-  int *bnd, *cnt, *ctl;
+  int *bnd, *cnt, *ctl, *tstart, *tf, *tl;
+  float *P;
+  float4 *xs;
   double *red;
   float *ev_t, *ev_w;
   uint16_t *ev_u;
@@ -200,6 +245,8 @@ struct Sm {
     red = (double *)(base + c.red); ctl = (int *)(base + c.ctl);
     ev_t = (float *)(base + c.ev_t); ev_w = (float *)(base + c.ev_w);
     ev_u = (uint16_t *)(base + c.ev_u);
+    tstart = (int *)(base + c.tstart); tf = (int *)(base + c.tf); tl = (int *)(base + c.tl);
+    P = (float *)(base + c.P); xs = (float4 *)(base + c.xs);
   }
 };
 

@@ -205,14 +205,16 @@ def test_invalid_windows_report_status(mdhp, orc, wl):
     assert gpu["status"][-1] == 0
 
 
+@pytest.mark.parametrize("path", ["auto", "recursion"])
 @pytest.mark.parametrize("optimizer", [0, 1])
-def test_fit_matches_oracle_fixed_iterations(mdhp, orc, wl, optimizer):
+def test_fit_matches_oracle_fixed_iterations(mdhp, orc, wl, optimizer, path):
     bt = wl.make_workload(2, B=10, seed=202)
     M, B = bt.M, bt.B
     iters = 60
     lr = 1e-2 if optimizer == 0 else 3e-3
     db = mdhp.DeviceBatch.from_host(bt, "cuda")
     plan = mdhp.Plan(M, 0, B, int(bt.counts.max()))
+    plan.set_path(path)
     mu = torch.zeros(B, M, device="cuda")
     alpha = torch.zeros(B, M, M, device="cuda")
     beta = torch.from_numpy(bt.beta).cuda()
