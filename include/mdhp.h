@@ -208,6 +208,35 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
 #define MDHP_PATH_RECURSION 1
 mdhp_status mdhp_plan_set_path(mdhp_plan *plan, int32_t path);
 
+/*
+ * Batched fit without a plan and without allocating device memory.  (An
+ * addition of this library; the paper has no counterpart.)
+ *
+ * For callers that cannot call cudaMalloc: processes whose device memory is
+ * owned by another framework's pooling allocator, deployments that forbid
+ * allocation after start-up (a detector fitting every incoming window in a
+ * vehicle, say), or threads that must not risk the implicit synchronisation
+ * of an allocation.  It runs the same iteration as mdhp_fit_batch (the event
+ * recursion kernels, windows taken longest first by length bucket) and
+ * returns the same results within rounding, but keeps its work queue and
+ * window order in a fixed device array compiled into the library.
+ *   - B is limited to MDHP_NOALLOC_MAX_WINDOWS; larger batches get MDHP_E_ARG
+ *     (split them).  opts->init must be 0 or 1 (no learned initializer).
+ *   - Arguments and outputs as for mdhp_fit_batch; batch->max_events, when
+ *     known and small enough, stages windows in shared memory.
+ *   - The array (about 256 KB) is held by every GPU that loads the library
+ *     until the process exits.  The first call on each device looks up its
+ *     address (cudaGetSymbolAddress with that device current); make that first
+ *     call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (different
+ *     streams or host threads on one device) race and must be serialised by
+ *     the caller.  Each call clears what it needs before use.
+ */
+#define MDHP_NOALLOC_MAX_WINDOWS 65536
+mdhp_status mdhp_fit_batch_noalloc(const mdhp_batch *batch, const mdhp_fit_opts *opts, float *mu,
+                                   float *alpha, float *beta, double *loglik, int32_t *iters,
+                                   int32_t *win_status, void *stream);
+
 /* Text of the last error in this thread (static storage). */
 const char *mdhp_last_error(void);
 

@@ -10,6 +10,8 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(_HERE, "_build", "libmdhp.so")
 
+NOALLOC_MAX_WINDOWS = 65536  # MDHP_NOALLOC_MAX_WINDOWS in include/mdhp.h
+
 OK, E_ARG, E_UNSORTED, E_ID_RANGE, E_TIME_RANGE, E_NONFINITE, E_MAXITER, E_TIMEOUT, E_CUDA, \
     E_NOMEM, E_UNSUPPORTED = range(11)
 STATUS_NAMES = ["OK", "E_ARG", "E_UNSORTED", "E_ID_RANGE", "E_TIME_RANGE", "E_NONFINITE",
@@ -47,6 +49,8 @@ SIGNATURES = [
     ("mdhp_plan_get_shape", ctypes.c_int, [P, P, P, P]),
     ("mdhp_plan_set_shape", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     ("mdhp_plan_set_path", ctypes.c_int, [P, ctypes.c_int32]),
+    ("mdhp_fit_batch_noalloc", ctypes.c_int, [ctypes.POINTER(MdhpBatch), ctypes.POINTER(MdhpFitOpts),
+                                              P, P, P, P, P, P, P]),
     ("mdhp_last_error", ctypes.c_char_p, []),
     ("mdhp_version", ctypes.c_int32, []),
 ]

@@ -24,6 +24,9 @@ static mdhp_status fail(mdhp_status s, const char *fmt, ...) {
   return s;
 }
 
+// Lets other translation units of the library report through mdhp_last_error().
+void record_error(const char *msg) { g_last_error = msg; }
+
 static mdhp_status cuda_check(const char *what) {
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MDHP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));

@@ -17,6 +17,7 @@ LlgFn get_llg(int M, int SPL, int BM, bool learn, bool stage);
 FitFn get_fit(int M, int SPL, int BM, bool learn, bool stage);
 WgFn get_wg(int M, int BM);
 FitFn get_fitx(int M, int BM, bool xs);
+void record_error(const char *msg);
 
 #define MDHP_DECLARE_M(MV)                                                   \
   LlgFn get_llg_m##MV(int SPL, int BM, bool learn, bool stage);              \
