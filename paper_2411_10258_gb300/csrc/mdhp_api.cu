@@ -162,7 +162,7 @@ struct mdhp_plan {
   int timing = 0, timed = 0;
   // decoupled fixed-beta fit: per-CTA feature scratch for windows of up to xcap events
   float4 *xbuf = nullptr;
-  int xcap = 0, xgrid = 0, xnt = 128;
+  int xcap = 0, xgrid = 0, xnt = 128;  // xnt: threads per window of the decoupled kernels
   int xres = 0, xrgrid = 0;  // windows of <= xres events keep their features in shared memory
   int xres_max = 0;          // largest shared-memory class the device allows
   int use_x = 1;  // 0 forces the recursion kernels (for tests and comparisons)
@@ -291,6 +291,7 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
   p->max_windows = max_windows;
   p->max_events = max_events_per_window;
   p->shape = default_shape(p->Mt);
+  p->xnt = p->Mt >= 32 ? 64 : 128;  // measured on the 4,096 x M=16 and 65,536 x M=32 workloads
   bool ok = true;
   ok &= cudaMalloc(&p->keys, sizeof(int) * max_windows) == cudaSuccess;
   ok &= cudaMalloc(&p->keys_sorted, sizeof(int) * max_windows) == cudaSuccess;
@@ -304,12 +305,18 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
   }
   if (ok && p->Mt <= 32 && max_events_per_window > 0 && max_events_per_window < (1 << 26)) {
     FitFn fx = get_fitx(p->Mt, beta_mode, false);
-    const Carve cx = make_carve_x(p->Mt, p->xnt, 0, true);
-    int occ = 0;
-    if (fx && prepare_kernel((const void *)fx, cx.total) == MDHP_OK &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fx, p->xnt, cx.total) == cudaSuccess &&
-        occ > 0) {
-      p->xgrid = num_sms() * occ;
+    // scratch slots for the largest resident grid over the supported block sizes
+    int slots = 0;
+    for (int nt = 64; nt <= 256; nt *= 2) {
+      const Carve cx = make_carve_x(p->Mt, nt, 0, true);
+      int occ = 0;
+      if (fx && prepare_kernel((const void *)fx, cx.total) == MDHP_OK &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fx, nt, cx.total) == cudaSuccess &&
+          num_sms() * occ > slots)
+        slots = num_sms() * occ;
+    }
+    if (slots > 0) {
+      p->xgrid = slots;
       p->xcap = (int)max_events_per_window;
       const size_t bytes = (size_t)p->xgrid * (size_t)(p->Mt / 4) * (size_t)p->xcap * sizeof(float4);
       if (cudaMalloc(&p->xbuf, bytes) != cudaSuccess) {
@@ -333,9 +340,10 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
           occr > 0) {
         p->xres_max = cap;
         p->xrgrid = num_sms() * occr;
-        // measured default: for M <= 16 the shared-memory class takes the L1
-        // capacity the global-feature class relies on, so it is off
-        p->xres = p->Mt >= 32 ? cap : 0;
+        // measured default: streaming every window's features through L1/L2
+        // beats keeping the short windows' features in shared memory (which
+        // takes the L1 capacity the streaming class relies on)
+        p->xres = 0;
       }
     }
     cudaGetLastError();
@@ -409,6 +417,7 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *p, int32_t nt, int32_t spl, int32_t c
     return fail(MDHP_E_UNSUPPORTED, "threads per chunk %d not built for M<=%d", spl, p->Mt);
   if (cutoff < 0) return fail(MDHP_E_ARG, "cutoff < 0");
   p->shape = Shape{nt, spl, cutoff};
+  if (nt >= 64 && nt <= 256 && (nt & (nt - 1)) == 0 && nt >= p->Mt) p->xnt = nt;
   p->xres = cutoff < p->xres_max ? (cutoff / 32) * 32 : p->xres_max;
   if (p->xres < 64) p->xres = 0;
   return MDHP_OK;
@@ -451,7 +460,13 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     return cuda_check("radix sort");
   const bool xpath = p->use_x && !learn && p->xbuf && bound > 0 && bound <= p->xcap;
   // decoupled path: windows longer than the shared-memory class form the first range
-  const int xcut = p->xres > 0 ? p->xres : -1;
+  int xcut = -1;
+  if (p->xres > 0) {
+    const int fixed = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1).total;
+    const int fit = ((max_dyn_smem() - 1024 - fixed) / (p->Mt * 4)) / 32 * 32;
+    xcut = p->xres < fit ? p->xres : fit;
+    if (xcut < 64) xcut = -1;
+  }
   k_split<<<1, 32, 0, st>>>(p->keys_sorted, B, xpath ? xcut : ev_cap, (xpath || need_long) ? 1 : 0,
                             p->ctl);
   if ((s = cuda_check("k_split")) != MDHP_OK) return s;
@@ -466,13 +481,20 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   a.alpha_floor = o->alpha_floor; a.beta_floor = o->beta_floor; a.b1 = o->adam_b1;
   a.b2 = o->adam_b2; a.eps = o->adam_eps; a.tol = o->tol;
 
+  int xres = p->xres;
+  if (xpath && xres > 0) {  // the largest class that fits this block size
+    const int fixed = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1).total;
+    const int fit = ((max_dyn_smem() - 1024 - fixed) / (p->Mt * 4)) / 32 * 32;
+    if (xres > fit) xres = fit;
+    if (xres < 64) xres = 0;
+  }
   if (xpath) {
     // long windows: features in the per-CTA global scratch (side stream);
     // short windows: features in shared memory (this stream); both queues
     // are taken longest first
     FitArgs ax = a;
     ax.xbuf = p->xbuf;
-    const bool any_long = !(p->xres > 0 && bound <= p->xres);
+    const bool any_long = !(xres > 0 && bound <= xres);
     if (p->timing) cudaEventRecord(p->ev_t0, st);
     if (any_long) {
       FitFn fx = get_fitx(p->Mt, p->beta_mode, false);
@@ -483,24 +505,30 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
       al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1);
       if ((s = prepare_kernel((const void *)fx, al.carve.total)) != MDHP_OK) return s;
       cudaStream_t ls = st;
-      if (p->xres > 0) {
+      if (xres > 0) {
         cudaEventRecord(p->ev_fork, st);
         cudaStreamWaitEvent(p->side, p->ev_fork, 0);
         ls = p->side;
       }
-      fx<<<p->xgrid, p->xnt, al.carve.total, ls>>>(al);
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fx, p->xnt, al.carve.total);
+      int gl = num_sms() * (occ > 0 ? occ : 1);
+      if (gl > p->xgrid) gl = p->xgrid;
+      fx<<<gl, p->xnt, al.carve.total, ls>>>(al);
       if ((s = cuda_check("k_fit_x (global features)")) != MDHP_OK) return s;
-      if (p->xres > 0) cudaEventRecord(p->ev_join, p->side);
+      if (xres > 0) cudaEventRecord(p->ev_join, p->side);
     }
-    if (p->xres > 0) {
+    if (xres > 0) {
       FitFn fr = get_fitx(p->Mt, p->beta_mode, true);
       FitArgs ar = ax;
       ar.queue = p->ctl + 1;
       ar.range = p->ctl + 4;
-      ar.ev_cap = p->xres;
-      ar.carve = make_carve_x(p->Mt, p->xnt, p->xres, o->optimizer == 1);
+      ar.ev_cap = xres;
+      ar.carve = make_carve_x(p->Mt, p->xnt, xres, o->optimizer == 1);
       if ((s = prepare_kernel((const void *)fr, ar.carve.total)) != MDHP_OK) return s;
-      int grid = p->xrgrid;
+      int occr = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occr, fr, p->xnt, ar.carve.total);
+      int grid = num_sms() * (occr > 0 ? occr : 1);
       if (grid > B) grid = B;
       fr<<<grid, p->xnt, ar.carve.total, st>>>(ar);
       if ((s = cuda_check("k_fit_x (shared features)")) != MDHP_OK) return s;

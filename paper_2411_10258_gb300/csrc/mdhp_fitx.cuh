@@ -175,7 +175,7 @@ __device__ __forceinline__ float xseg_sum(int i, int j, const Sm<M> &sm) {
 }
 
 template <int M, int BM, bool XS>
-__global__ void __launch_bounds__(128, (M >= 32 ? 3 : 4)) k_fit_x(FitArgs a) {
+__global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   Sm<M> sm;
   sm.bind(smem, a.carve);
