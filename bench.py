@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     return ap.parse_args()
 
 
@@ -121,11 +123,16 @@ def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
 
 
 def flops_per_event_iter(M: int) -> int:
-    """Algorithmic FP32 work of one event in one evaluation (scalar, fixed beta):
-    decay of M states (M), the dot alpha_u . R (2M), d/dalpha_u accumulation
-    r R_j and its sum (2M), plus lambda, 1/lambda bookkeeping and the Kahan
-    sum of ln lambda (8)."""
-    return 5 * M + 8
+    """Algorithmic FP32 work of one event in one evaluation of the decoupled
+    fixed-beta fit (features x_n = R(t_n) precomputed once per window):
+    lambda = mu + alpha_u . x_n (2M), d/dalpha_u += r x_n (2M), plus the
+    d/dmu sum, 1/lambda and the Kahan sum of ln lambda (8)."""
+    return 4 * M + 8
+
+
+def feature_bytes_per_event_iter(M: int) -> int:
+    """Bytes of features each evaluation reads per event (float32 x_n)."""
+    return 4 * M
 
 
 def make_inputs(args, rank):
@@ -291,11 +298,14 @@ def run_ours(args):
                        "l2": "flushed (256 MB write) before every timed step"},
             "llg_events_per_s": llg_events_per_s,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_fit (staged)",
+                         "frac": achieved / peak, "traffic": args.traffic,
+                         "kernel": "k_fit_x (decoupled features streamed through L1/L2)",
                          "peak_source": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 FLOP x "
                                         f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)",
-                         "flops_per_event_iteration": flops_per_event_iter(M)},
+                         "flops_per_event_iteration": flops_per_event_iter(M),
+                         "feature_bytes_per_event_iteration": feature_bytes_per_event_iter(M),
+                         "feature_read_gbs": events_iters * feature_bytes_per_event_iter(M)
+                                             / (kern_avg / 1000.0) / 1e9},
             "gpu_launches": 3 * args.steps,
             "invalid_windows": bad,
             "clocks": clocks, "e2e": e2e}

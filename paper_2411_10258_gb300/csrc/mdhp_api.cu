@@ -291,7 +291,7 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
   p->max_windows = max_windows;
   p->max_events = max_events_per_window;
   p->shape = default_shape(p->Mt);
-  p->xnt = p->Mt >= 32 ? 64 : 128;  // measured on the 4,096 x M=16 and 65,536 x M=32 workloads
+  p->xnt = 64;  // measured best on the 4,096 x M=16 and M=32 workloads (64/128/256 swept)
   bool ok = true;
   ok &= cudaMalloc(&p->keys, sizeof(int) * max_windows) == cudaSuccess;
   ok &= cudaMalloc(&p->keys_sorted, sizeof(int) * max_windows) == cudaSuccess;
@@ -318,7 +318,10 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
     if (slots > 0) {
       p->xgrid = slots;
       p->xcap = (int)max_events_per_window;
-      const size_t bytes = (size_t)p->xgrid * (size_t)(p->Mt / 4) * (size_t)p->xcap * sizeof(float4);
+      // per slot (xcap + 2 * 256) rows: the step-major layout pads each
+      // window to L * threads with L odd (see mdhp_fitx.cuh)
+      const size_t bytes = (size_t)p->xgrid * (size_t)(p->Mt / 4) * (size_t)(p->xcap + 512) *
+                           sizeof(float4);
       if (cudaMalloc(&p->xbuf, bytes) != cudaSuccess) {
         cudaGetLastError();
         p->xbuf = nullptr;  // the recursion kernels still work without it

@@ -23,20 +23,27 @@
 
 namespace mdhp {
 
-// Feature layout: in shared memory, slices as planes [q][pos] (a warp's lanes
-// read positions an odd stride apart: distinct bank groups); in global memory,
-// rows [pos][q] (a lane's features are contiguous, so its L1 lines are reused
-// by its next position).
+// Feature layout.  Thread t owns sorted positions [t L, t L + L) and reads
+// them in order, step k = pos - t L.  In shared memory the slices are planes
+// [q][pos] (the lanes' positions are an odd stride L apart: distinct bank
+// groups).  In global memory they are stored step-major, [k][q][t]: at each
+// step a warp's 32 lanes read 512 contiguous bytes per float4 slice (4 cache
+// lines), where a position-major layout would touch 32 lines per load.
+struct XMap {
+  int L, NT;
+};
 template <bool XS>
-__device__ __forceinline__ int xidx(int q, int pos, int xcap, int NQ) {
-  return XS ? q * xcap + pos : pos * NQ + q;
+__device__ __forceinline__ int xidx(int q, int pos, int xcap, int NQ, XMap m) {
+  if (XS) return q * xcap + pos;
+  const int t = pos / m.L, k = pos - t * m.L;
+  return (k * NQ + q) * m.NT + t;
 }
 
 // Counting sort of the window's events by type and the feature walk.
 // Needs bnd/anc (NT chunks), encR (entering states), cnt (events per type).
 // Writes X[q * xcap + pos] (float4 slices of x_n) and tstart[0..M].
 template <int M, int BM, bool XS, typename EV, typename XP>
-__device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, int xcap) {
+__device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, int xcap, XMap m) {
   constexpr int AP = M + 4;
   constexpr int NQ = M / 4;
   const int tid = threadIdx.x, NT = blockDim.x, NC = NT;
@@ -85,7 +92,7 @@ __device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, in
     ctr[un * NC + c] = pos + 1;
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
-      X[xidx<XS>(q, pos, xcap, NQ)] =
+      X[xidx<XS>(q, pos, xcap, NQ, m)] =
           make_float4(wk.R[4 * q], wk.R[4 * q + 1], wk.R[4 * q + 2], wk.R[4 * q + 3]);
   }
   __syncthreads();
@@ -94,8 +101,8 @@ __device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, in
 // One evaluation over the sorted features: this thread's range [p0, p1),
 // starting in type i0.  Segment sums go to P[(tid + i) * (M + 4) + 0..M].
 template <int M, bool XS, typename XP>
-__device__ __forceinline__ void xpass(int p0, int p1, int i0, XP X, int xcap, const Sm<M> &sm,
-                                      float &Ls, float &Lc) {
+__device__ __forceinline__ void xpass(int p0, int p1, int i0, XP X, int xcap, XMap m,
+                                      const Sm<M> &sm, float &Ls, float &Lc) {
   constexpr int NQ = M / 4;
   constexpr int AP = M + 4;
   constexpr int PP = M + 4;
@@ -113,14 +120,14 @@ __device__ __forceinline__ void xpass(int p0, int p1, int i0, XP X, int xcap, co
   float gm = 0.f;
   float4 xn[NQ];  // next position's features, loaded one step ahead
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) xn[q] = X[xidx<XS>(q, p0, xcap, NQ)];
+  for (int q = 0; q < NQ; ++q) xn[q] = X[xidx<XS>(q, p0, xcap, NQ, m)];
   for (int p = p0; p < p1; ++p) {
     float4 x[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) x[q] = xn[q];
     if (p + 1 < p1) {
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) xn[q] = X[xidx<XS>(q, p + 1, xcap, NQ)];
+      for (int q = 0; q < NQ; ++q) xn[q] = X[xidx<XS>(q, p + 1, xcap, NQ, m)];
     }
     while (p >= te) {  // leave type i (types with no events are passed over)
       float4 *slot = reinterpret_cast<float4 *>(sm.P + (tid + i) * PP);
@@ -186,7 +193,8 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
   const int nupd = Mrt + Mrt * Mrt;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int xcap = a.ev_cap;
-  float4 *Xg = XS ? nullptr : a.xbuf + (size_t)blockIdx.x * (M / 4) * (size_t)xcap;
+  // global slot: (xcap + 2 NT) rows, enough for L * NT with the odd rounding of L
+  float4 *Xg = XS ? nullptr : a.xbuf + (size_t)blockIdx.x * (M / 4) * (size_t)(xcap + 2 * NT);
   for (;;) {
     if (tid == 0) sm.ctl[1] = atomicAdd(a.queue, 1);
     __syncthreads();
@@ -230,12 +238,13 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     const EvG ev{tg, ug, wg};
     setup_chunks(NT, N, T, ev, sm.bnd, sm.anc);
     prepare_states<M, 1, BM, false>(NT, ev, Mrt, sm);
-    if (XS) build_features<M, BM, true>(N, ev, Mrt, sm, sm.xs, xcap);
-    else build_features<M, BM, false>(N, ev, Mrt, sm, Xg, xcap);
     // thread ranges over the sorted features; an odd length keeps the
-    // lanes' float4 reads on distinct bank groups
+    // lanes' shared-memory float4 reads on distinct bank groups
     int L = (N + NT - 1) / NT;
     L = max(L | 1, 1);
+    const XMap xm{L, NT};
+    if (XS) build_features<M, BM, true>(N, ev, Mrt, sm, sm.xs, xcap, xm);
+    else build_features<M, BM, false>(N, ev, Mrt, sm, Xg, xcap, xm);
     const int p0 = min(tid * L, N), p1 = min(p0 + L, N);
     int i0 = 0;
     while (i0 < M - 1 && sm.tstart[i0 + 1] <= p0) ++i0;
@@ -251,8 +260,8 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     float b1t = 1.f, b2t = 1.f;
     for (k = 0; k < a.max_iters; ++k) {
       float Ls = 0.f, Lc = 0.f;
-      if (XS) xpass<M, true>(p0, p1, i0, (const float4 *)sm.xs, xcap, sm, Ls, Lc);
-      else xpass<M, false>(p0, p1, i0, (const float4 *)Xg, xcap, sm, Ls, Lc);
+      if (XS) xpass<M, true>(p0, p1, i0, (const float4 *)sm.xs, xcap, xm, sm, Ls, Lc);
+      else xpass<M, false>(p0, p1, i0, (const float4 *)Xg, xcap, xm, sm, Ls, Lc);
       // Part2 + Part3 and the block sums (ends with a barrier)
       float Ps = 0.f, Pc = 0.f;
       for (int p = tid; p < M + M * M; p += NT) {  // padded entries hold zeros
