@@ -130,7 +130,7 @@ mdhp_status mdhp_loglik_grad(const mdhp_batch *batch, const float *mu, const flo
  *              1: cold start, mu_i = 0.5 max(N_i,1) / T_span, alpha_ij = 0.5 beta_ij / M
  *                 (spectral radius of alpha/beta = 0.5); beta as passed in
  *              2: learned initializer (the plan must hold a model, see
- *                 mdhp_plan_set_init_model); beta as passed in
+ *                 mdhp_plan_set_init_model; M <= 32); beta as passed in
  */
 typedef struct {
   int32_t optimizer;
@@ -197,6 +197,65 @@ mdhp_status mdhp_plan_get_shape(const mdhp_plan *plan, int32_t *threads_per_wind
                                 int32_t *threads_per_chunk, int32_t *smem_cutoff_events);
 mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
                                 int32_t threads_per_chunk, int32_t smem_cutoff_events);
+
+/*
+ * Learned warm start (an addition of this library; the paper starts its
+ * descent from an unstated point).  A 4-layer MLP (BF16 weights and
+ * activations, FP32 accumulation, ReLU, width `hidden`) maps per-window
+ * features to a starting point (mu, alpha) for the fit; it is trained on the
+ * GPU by mdhp_init_train_step on windows whose targets the fit itself produced.
+ *
+ * Features of a window (feature_dim = M + 32 M^2 + 3, zero-padded to a multiple
+ * of 64, BF16 row-major [B][feature_dim]): the share N_i / N of each type; for
+ * every ordered pair (i, j) a 32-bin histogram of log2(gap * N / T), gap = time
+ * from each type-i event back to the last strictly earlier type-j event, bin
+ * floor(log2) + 16 clamped to [0, 31], normalised to sum 1; log N, log T, beta.
+ * mu_cold [B][M] receives the fit's cold start 0.5 max(N_i, 1) / T.
+ * Head: mu_i = mu_cold_i exp(clamp(y_i, -6, 6)), alpha_ij = beta_ij / M * softplus(y_ij).
+ * Training loss per window (mean over the batch):
+ *   sum_i (y_i - log(mu*_i / mu_cold_i))^2 + sum_ij (softplus(y_ij) - alpha*_ij M / beta_ij)^2.
+ * M is limited to 1..32.
+ */
+typedef struct mdhp_init_model mdhp_init_model;
+
+/* Allocates weights (FP32 master + BF16 copy, uniform(+-1/sqrt(fan_in)) from
+ * `seed`, zero biases), AdamW moments and activations for batches of up to
+ * max_batch windows. */
+mdhp_status mdhp_init_model_create(mdhp_init_model **model, int32_t M, int32_t hidden,
+                                   int32_t max_batch, uint64_t seed);
+void mdhp_init_model_destroy(mdhp_init_model *model);
+
+/* Sizes, and the device address of the flat FP32 parameter vector (layer l:
+ * W_l [out][in] row-major then b_l [out], each block 256-aligned); after
+ * writing it (checkpoint load) call mdhp_init_model_sync_params. */
+mdhp_status mdhp_init_model_info(const mdhp_init_model *model, int32_t *feature_dim,
+                                 int32_t *out_dim, int64_t *num_params, float **params_device);
+mdhp_status mdhp_init_model_sync_params(mdhp_init_model *model, void *stream);
+
+/* Features of every window of `batch` (beta per batch->beta_mode). */
+mdhp_status mdhp_init_features(const mdhp_batch *batch, const float *beta, void *features_bf16,
+                               float *mu_cold, void *stream);
+
+/* Network output y [B][out_dim] (FP32) for precomputed features. */
+mdhp_status mdhp_init_forward(mdhp_init_model *model, const void *features_bf16, int32_t B,
+                              float *out, void *stream);
+
+/* Features -> network -> head: writes mu [B][M] and alpha [B][M][M]. */
+mdhp_status mdhp_init_predict(mdhp_init_model *model, const mdhp_batch *batch, const float *beta,
+                              float *mu, float *alpha, void *stream);
+
+/* One AdamW step (b1 0.9, b2 0.999, eps 1e-8, decay on matrices only) on a
+ * batch of B <= max_batch precomputed feature rows with targets mu* [B][M],
+ * alpha* [B][M][M]; beta is [B] (beta_stride 1) or [B][M] (beta_stride M).
+ * loss_out (device float, nullable) receives the batch loss before the step. */
+mdhp_status mdhp_init_train_step(mdhp_init_model *model, const void *features_bf16,
+                                 const float *mu_cold, const float *beta, int32_t beta_stride,
+                                 const float *mu_target, const float *alpha_target, int32_t B,
+                                 float lr, float weight_decay, float *loss_out, void *stream);
+
+/* Attach a trained model to a plan: mdhp_fit_batch with opts->init == 2 then
+ * predicts the starting point with it (the plan does not own the model). */
+mdhp_status mdhp_plan_set_init_model(mdhp_plan *plan, mdhp_init_model *model);
 
 /* Kernel family used by mdhp_fit_batch for fixed beta:
  *   MDHP_PATH_AUTO (0)      decoupled features when the plan has scratch for

@@ -166,6 +166,7 @@ struct mdhp_plan {
   int xres = 0, xrgrid = 0;  // windows of <= xres events keep their features in shared memory
   int xres_max = 0;          // largest shared-memory class the device allows
   int use_x = 1;  // 0 forces the recursion kernels (for tests and comparisons)
+  mdhp_init_model *model = nullptr;  // learned initializer (not owned)
 };
 
 extern "C" {
@@ -397,6 +398,12 @@ float mdhp_plan_last_fit_ms(mdhp_plan *p) {
   return ms;
 }
 
+mdhp_status mdhp_plan_set_init_model(mdhp_plan *p, mdhp_init_model *model) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  p->model = model;
+  return MDHP_OK;
+}
+
 mdhp_status mdhp_plan_set_path(mdhp_plan *p, int32_t path) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
   if (path != MDHP_PATH_AUTO && path != MDHP_PATH_RECURSION) return fail(MDHP_E_ARG, "path %d", path);
@@ -440,13 +447,26 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   if (o->max_iters < 1) return fail(MDHP_E_ARG, "max_iters < 1");
   if (o->optimizer != 0 && o->optimizer != 1) return fail(MDHP_E_ARG, "optimizer %d", o->optimizer);
   if (o->init < 0 || o->init > 2) return fail(MDHP_E_ARG, "init %d", o->init);
-  if (o->init == 2) return fail(MDHP_E_UNSUPPORTED, "learned initializer not loaded in this plan");
+  if (o->init == 2 && !p->model)
+    return fail(MDHP_E_ARG, "init = 2 needs a model (mdhp_plan_set_init_model)");
   if (o->patience < 1) return fail(MDHP_E_ARG, "patience < 1");
   if (!mu || !alpha || !beta || !loglik || !iters || !win_status)
     return fail(MDHP_E_ARG, "NULL parameter/output pointer");
   const int B = batch->B;
   if (B == 0) return MDHP_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  mdhp_fit_opts oo = *o;
+  bool t0_done = false;  // the timed region starts before the initializer when it runs
+  if (o->init == 2) {  // learned starting point, then the fit from it
+    if (p->timing) {
+      cudaEventRecord(p->ev_t0, st);
+      t0_done = true;
+    }
+    const mdhp_status si = mdhp_init_predict(p->model, batch, beta, mu, alpha, stream);
+    if (si != MDHP_OK) return si;
+    oo.init = 0;
+  }
+  o = &oo;
   const Shape sh = p->shape;
   const int NC = sh.nt / sh.spl;
   const bool learn = o->fit_beta != 0;
@@ -498,7 +518,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     FitArgs ax = a;
     ax.xbuf = p->xbuf;
     const bool any_long = !(xres > 0 && bound <= xres);
-    if (p->timing) cudaEventRecord(p->ev_t0, st);
+    if (p->timing && !t0_done) cudaEventRecord(p->ev_t0, st);
     if (any_long) {
       FitFn fx = get_fitx(p->Mt, p->beta_mode, false);
       FitArgs al = ax;
@@ -543,7 +563,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     }
     return MDHP_OK;
   }
-  if (p->timing) cudaEventRecord(p->ev_t0, st);
+  if (p->timing && !t0_done) cudaEventRecord(p->ev_t0, st);
   if (need_long) {
     FitFn fl = get_fit(p->Mt, sh.spl, p->beta_mode, learn, false);
     if (!fl) return fail(MDHP_E_UNSUPPORTED, "no streamed fit kernel for this shape");

@@ -1,0 +1,623 @@
+// Learned warm start for MDHP-GDS: per-window features, a 4-layer BF16 MLP
+// (FP32 accumulate) trained on the GPU by the kernels below, and a head that
+// maps its output to a starting point (mu, alpha) for the fit.  The paper has
+// no initializer; the fit it starts is the paper's (Sec. IV-B).
+//
+// Features of a window (K = M + 32 M^2 + 3 values, zero-padded to K0):
+//   N_i / N                          event share of each type
+//   h_ij[b], b = 0..31               for every event of type i, the gap to the
+//                                    last earlier event of type j (strictly
+//                                    earlier: a tie group does not see
+//                                    itself), as bin floor(log2(gap N / T)) + 16
+//                                    clamped to [0, 31]; each (i, j) histogram
+//                                    divided by its total
+//   log N, log T, beta
+// Network: X [B, K0] -> 4 layers (ReLU between) -> Y [B, M + M^2].
+// Head:    mu_i = mu_cold_i exp(clamp(y_i, -6, 6)), alpha_ij = (beta / M) softplus(y_ij),
+//          mu_cold the fit's cold start 0.5 max(N_i, 1) / T.
+// Loss (training, per window): sum_i (y_i - log(mu*_i / mu_cold_i))^2 +
+//          sum_ij (softplus(y_ij) - alpha*_ij M / beta)^2, averaged over windows.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "mdhp.h"
+#include "mdhp_dispatch.h"
+
+namespace mdhp {
+
+constexpr int kBins = 32;
+
+__host__ __device__ inline int init_k0(int M) {
+  const int K = M + kBins * M * M + 3;
+  return (K + 63) / 64 * 64;
+}
+
+// ---------------------------------------------------------------------------
+// Features.  One CTA per window, NT threads = NT chunks of the window.
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(128) k_features(const int64_t *offsets, const float *t,
+                                                  const int16_t *id, const float *Tspan,
+                                                  const float *beta, int beta_stride, int Mrt,
+                                                  int K0, __nv_bfloat16 *X, float *aux) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int *hist = reinterpret_cast<int *>(smem);            // [M][M][kBins]
+  float *lastc = reinterpret_cast<float *>(hist + M * M * kBins);  // [NT][M]
+  int *cnt = reinterpret_cast<int *>(lastc + blockDim.x * M);      // [M]
+  const int b = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+  const int64_t o0 = offsets[b];
+  const int N = (int)(offsets[b + 1] - o0);
+  const float T = Tspan[b];
+  const float *tt = t + o0;
+  const int16_t *uu = id + o0;
+  for (int p = tid; p < M * M * kBins; p += NT) hist[p] = 0;
+  for (int j = tid; j < M; j += NT) cnt[j] = 0;
+  __syncthreads();
+  // chunk c = [b0, b1), boundaries moved past tie groups
+  const int c = tid;
+  int b0 = (int)(((long long)c * N) / NT), b1 = (int)(((long long)(c + 1) * N) / NT);
+  while (b0 > 0 && b0 < N && tt[b0] == tt[b0 - 1]) ++b0;
+  while (b1 > 0 && b1 < N && tt[b1] == tt[b1 - 1]) ++b1;
+  if (c == NT - 1) b1 = N;
+  // last time of each type inside the chunk
+  float lt[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) lt[j] = -INFINITY;
+  for (int n = b0; n < b1; ++n) {
+    const int u = (int)uu[n];
+    if (u >= 0 && u < Mrt) {
+#pragma unroll
+      for (int j = 0; j < M; ++j) lt[j] = (j == u) ? tt[n] : lt[j];
+      atomicAdd(&cnt[u], 1);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) lastc[c * M + j] = lt[j];
+  __syncthreads();
+  if (tid < M) {  // exclusive running max over chunks
+    float run = -INFINITY;
+    for (int cc = 0; cc < NT; ++cc) {
+      const float v = lastc[cc * M + tid];
+      lastc[cc * M + tid] = run;
+      run = fmaxf(run, v);
+    }
+  }
+  __syncthreads();
+  // histogram walk: gaps to the last earlier event of every type
+#pragma unroll
+  for (int j = 0; j < M; ++j) lt[j] = lastc[c * M + j];
+  const float scale = (T > 0.f && N > 0) ? (float)N / T : 1.f;
+  int gs = b0;
+  float tcur = (b0 < b1) ? tt[b0] : 0.f;
+  for (int n = b0; n < b1; ++n) {
+    const float tn = tt[n];
+    if (tn > tcur) {  // the previous tie group becomes history
+      for (int k = gs; k < n; ++k) {
+        const int u = (int)uu[k];
+#pragma unroll
+        for (int j = 0; j < M; ++j) lt[j] = (j == u) ? tt[k] : lt[j];
+      }
+      tcur = tn;
+      gs = n;
+    }
+    const int i = (int)uu[n];
+    if (i < 0 || i >= Mrt) continue;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      if (j < Mrt && lt[j] > -INFINITY) {
+        const float gap = (tn - lt[j]) * scale;
+        int bin = gap > 0.f ? (int)floorf(log2f(gap)) + kBins / 2 : 0;
+        bin = bin < 0 ? 0 : (bin >= kBins ? kBins - 1 : bin);
+        atomicAdd(&hist[(i * M + j) * kBins + bin], 1);
+      }
+    }
+  }
+  __syncthreads();
+  __nv_bfloat16 *row = X + (size_t)b * K0;
+  const float invN = N > 0 ? 1.f / (float)N : 0.f;
+  for (int p = tid; p < K0; p += NT) {
+    float v = 0.f;
+    if (p < Mrt) {
+      v = (float)cnt[p] * invN;
+    } else if (p >= M && p < M + M * M * kBins) {
+      const int q = p - M, pair = q / kBins;
+      const int i = pair / M, j = pair % M;
+      if (i < Mrt && j < Mrt) {
+        int tot = 0;
+        for (int k = 0; k < kBins; ++k) tot += hist[pair * kBins + k];
+        v = tot > 0 ? (float)hist[q] / (float)tot : 0.f;
+      }
+    } else if (p == M + M * M * kBins) {
+      v = logf((float)(N > 0 ? N : 1));
+    } else if (p == M + M * M * kBins + 1) {
+      v = logf(T > 0.f ? T : 1.f);
+    } else if (p == M + M * M * kBins + 2) {
+      v = beta[(int64_t)b * beta_stride];
+    }
+    row[p] = __float2bfloat16(v);
+  }
+  for (int i = tid; i < Mrt; i += NT) aux[(int64_t)b * Mrt + i] = 0.5f * (float)max(cnt[i], 1) / T;
+}
+
+// ---------------------------------------------------------------------------
+// BF16 GEMM on the tensor cores (mma.sync m16n8k16, FP32 accumulate).
+// C[m][n] = sum_k A(m,k) B(k,n), A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn].
+// CTA tile 64 x 64 x 32, 4 warps of 32 x 32.  Epilogue: + bias[n], ReLU,
+// FP32 and/or BF16 output (row-major, ldc), or accumulate into FP32.
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+  const __nv_bfloat16 *A, *B;
+  int64_t sam, sak, sbk, sbn;
+  int Mm, Nn, Kk;
+  const float *bias;
+  int relu, accumulate;
+  float *Cf;
+  __nv_bfloat16 *Cb;
+  int64_t ldc;
+};
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4],
+                                               const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
+  constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+  __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];  // [n][k]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int grp = lane >> 2, tig = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  for (int k0 = 0; k0 < g.Kk; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 128) {
+      const int r = e / BK, kk = e % BK;
+      const int m = m0 + r, k = k0 + kk;
+      As[r][kk] = (m < g.Mm && k < g.Kk) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : zero;
+    }
+    for (int e = tid; e < BN * BK; e += 128) {
+      const int r = e / BK, kk = e % BK;
+      const int n = n0 + r, k = k0 + kk;
+      Bs[r][kk] = (n < g.Nn && k < g.Kk) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int r = wm + a * 16 + grp;
+        af[a][0] = *reinterpret_cast<const uint32_t *>(&As[r][ks + tig * 2]);
+        af[a][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + tig * 2]);
+        af[a][2] = *reinterpret_cast<const uint32_t *>(&As[r][ks + tig * 2 + 8]);
+        af[a][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + tig * 2 + 8]);
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int n = wn + b * 8 + grp;
+        bfr[b][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][ks + tig * 2]);
+        bfr[b][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][ks + tig * 2 + 8]);
+      }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) mma_bf16_16816(acc[a][b], af[a], bfr[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = m0 + wm + a * 16 + grp + h * 8;
+        if (m >= g.Mm) continue;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int n = n0 + wn + b * 8 + tig * 2 + cc;
+          if (n >= g.Nn) continue;
+          float v = acc[a][b][h * 2 + cc];
+          const int64_t o = (int64_t)m * g.ldc + n;
+          if (g.accumulate) {
+            g.Cf[o] += v;
+            continue;
+          }
+          if (g.bias) v += g.bias[n];
+          if (g.relu) v = fmaxf(v, 0.f);
+          if (g.Cf) g.Cf[o] = v;
+          if (g.Cb) g.Cb[o] = __float2bfloat16(v);
+        }
+      }
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels of the training step
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-x)); }
+
+// Head: y [B, O] -> mu [B, M], alpha [B, M, M].
+__global__ void k_init_head(const float *Y, int O, const float *aux, const float *beta,
+                            int beta_stride, int Mrt, int Bn, float *mu, float *alpha) {
+  const int b = blockIdx.x;
+  if (b >= Bn) return;
+  const float *y = Y + (size_t)b * O;
+  for (int i = threadIdx.x; i < Mrt; i += blockDim.x) {
+    const float z = fminf(fmaxf(y[i], -6.f), 6.f);
+    mu[(int64_t)b * Mrt + i] = aux[(int64_t)b * Mrt + i] * expf(z);
+  }
+  for (int p = threadIdx.x; p < Mrt * Mrt; p += blockDim.x) {
+    const int j = p % Mrt;
+    const float bj = beta[(int64_t)b * beta_stride + (beta_stride == 1 ? 0 : j)];
+    alpha[(int64_t)b * Mrt * Mrt + p] = bj / (float)Mrt * softplusf(y[Mrt + p]);
+  }
+}
+
+// Loss and dL/dY (FP32 and BF16 copies); loss summed into *loss (atomic).
+__global__ void k_init_loss(const float *Y, int O, const float *aux, const float *beta,
+                            int beta_stride, int Mrt, int Bn, const float *mu_t,
+                            const float *alpha_t, float *dY, __nv_bfloat16 *dYb, float *loss) {
+  const int b = blockIdx.x;
+  if (b >= Bn) return;
+  const float inv = 1.f / (float)Bn;
+  float acc = 0.f;
+  for (int p = threadIdx.x; p < O; p += blockDim.x) {
+    float d = 0.f;
+    const float y = Y[(size_t)b * O + p];
+    if (p < Mrt) {
+      const float z = logf(fmaxf(mu_t[(int64_t)b * Mrt + p], 1e-20f) / aux[(int64_t)b * Mrt + p]);
+      const float e = y - z;
+      acc += e * e;
+      d = 2.f * e * inv;
+    } else if (p < Mrt + Mrt * Mrt) {
+      const int q = p - Mrt, j = q % Mrt;
+      const float bj = beta[(int64_t)b * beta_stride + (beta_stride == 1 ? 0 : j)];
+      const float a = alpha_t[(int64_t)b * Mrt * Mrt + q] * (float)Mrt / bj;
+      const float e = softplusf(y) - a;
+      acc += e * e;
+      d = 2.f * e * sigmoidf_(y) * inv;
+    }
+    dY[(size_t)b * O + p] = d;
+    dYb[(size_t)b * O + p] = __float2bfloat16(d);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * inv);
+}
+
+// dH = dH * (H > 0) in place (FP32) plus a BF16 copy.
+__global__ void k_relu_bwd(float *dH, const float *H, __nv_bfloat16 *dHb, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float v = H[i] > 0.f ? dH[i] : 0.f;
+    dH[i] = v;
+    dHb[i] = __float2bfloat16(v);
+  }
+}
+
+// db[n] += sum_b dY[b][n]
+__global__ void k_bias_grad(const float *dY, int Bn, int O, float *db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < O) {
+    float s = 0.f;
+    for (int b = 0; b < Bn; ++b) s += dY[(size_t)b * O + n];
+    db[n] += s;
+  }
+}
+
+// AdamW on the FP32 master weights, refreshing the BF16 copy of the matrices.
+__global__ void k_adamw(float *w, const float *g, float *m, float *v, __nv_bfloat16 *wb,
+                        const int *is_matrix, int64_t n, float lr, float b1, float b2, float eps,
+                        float wd, float c1, float c2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    float wi = w[i];
+    if (is_matrix[i >> 8]) wi -= lr * wd * wi;  // decoupled decay on matrices only
+    wi -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    wb[i] = __float2bfloat16(wi);
+  }
+}
+
+__global__ void k_f32_to_bf16(const float *w, __nv_bfloat16 *wb, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) wb[i] = __float2bfloat16(w[i]);
+}
+
+__global__ void k_init_uniform(float *w, __nv_bfloat16 *wb, int64_t n, float bound, uint64_t seed,
+                               uint64_t stream) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    // SplitMix64 of (seed, stream, i) -> uniform in [-bound, bound)
+    uint64_t z = seed + 0x9e3779b97f4a7c15ULL * (uint64_t)(i + 1) + (stream << 40);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    const float u = (float)(z >> 40) * (1.f / 16777216.f);
+    const float v = bound * (2.f * u - 1.f);
+    w[i] = v;
+    wb[i] = __float2bfloat16(v);
+  }
+}
+
+}  // namespace mdhp
+
+using namespace mdhp;
+
+struct mdhp_init_model {
+  int M, K0, H, O, max_batch, layers = 4;
+  int64_t off_w[4], off_b[4], nparams;
+  int din[4], dout[4];
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 master / grad / moments
+  __nv_bfloat16 *wb = nullptr;                                    // BF16 copy
+  int *is_matrix = nullptr;                                       // per 256-element block
+  __nv_bfloat16 *X = nullptr, *hb[4] = {};
+  float *h[4] = {}, *dh[4] = {}, *aux = nullptr, *loss = nullptr;
+  __nv_bfloat16 *dhb[4] = {};
+  int64_t step = 0;
+};
+
+static mdhp_status init_fail(mdhp_status s, const char *msg) {
+  record_error(msg);
+  return s;
+}
+
+static int grid1(int64_t n, int t = 256) { return (int)((n + t - 1) / t); }
+
+static void launch_gemm(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B,
+                        int64_t sbk, int64_t sbn, int Mm, int Nn, int Kk, const float *bias,
+                        int relu, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, int accumulate,
+                        cudaStream_t st) {
+  GemmArgs g{A, B, sam, sak, sbk, sbn, Mm, Nn, Kk, bias, relu, accumulate, Cf, Cb, ldc};
+  dim3 grid((Nn + 63) / 64, (Mm + 63) / 64);
+  k_gemm_bf16<<<grid, 128, 0, st>>>(g);
+}
+
+extern "C" {
+
+mdhp_status mdhp_init_model_create(mdhp_init_model **out, int32_t M, int32_t hidden,
+                                   int32_t max_batch, uint64_t seed) {
+  if (!out) return init_fail(MDHP_E_ARG, "mdhp_init_model_create: out NULL");
+  *out = nullptr;
+  if (M < 1 || M > 32) return init_fail(MDHP_E_ARG, "mdhp_init_model_create: M must be 1..32");
+  if (hidden < 64 || hidden > 4096 || hidden % 64)
+    return init_fail(MDHP_E_ARG, "mdhp_init_model_create: hidden must be a multiple of 64 in [64, 4096]");
+  if (max_batch < 1 || max_batch > 65536)
+    return init_fail(MDHP_E_ARG, "mdhp_init_model_create: max_batch must be 1..65536");
+  mdhp_init_model *p = new mdhp_init_model();
+  p->M = M;
+  p->K0 = init_k0(M);
+  p->H = hidden;
+  p->O = M + M * M;
+  p->max_batch = max_batch;
+  const int dims[5] = {p->K0, hidden, hidden, hidden, p->O};
+  int64_t off = 0;
+  for (int l = 0; l < 4; ++l) {
+    p->din[l] = dims[l];
+    p->dout[l] = dims[l + 1];
+    p->off_w[l] = off;
+    off += (int64_t)dims[l] * dims[l + 1];
+    off = (off + 255) / 256 * 256;
+    p->off_b[l] = off;
+    off += dims[l + 1];
+    off = (off + 255) / 256 * 256;
+  }
+  p->nparams = off;
+  bool ok = true;
+  ok &= cudaMalloc(&p->w, off * 4) == cudaSuccess;
+  ok &= cudaMalloc(&p->g, off * 4) == cudaSuccess;
+  ok &= cudaMalloc(&p->m, off * 4) == cudaSuccess;
+  ok &= cudaMalloc(&p->v, off * 4) == cudaSuccess;
+  ok &= cudaMalloc(&p->wb, off * 2) == cudaSuccess;
+  ok &= cudaMalloc(&p->is_matrix, (off / 256) * 4) == cudaSuccess;
+  ok &= cudaMalloc(&p->X, (size_t)max_batch * p->K0 * 2) == cudaSuccess;
+  ok &= cudaMalloc(&p->aux, (size_t)max_batch * M * 4) == cudaSuccess;
+  ok &= cudaMalloc(&p->loss, 4) == cudaSuccess;
+  for (int l = 0; l < 4; ++l) {
+    ok &= cudaMalloc(&p->h[l], (size_t)max_batch * p->dout[l] * 4) == cudaSuccess;
+    ok &= cudaMalloc(&p->hb[l], (size_t)max_batch * p->dout[l] * 2) == cudaSuccess;
+    ok &= cudaMalloc(&p->dh[l], (size_t)max_batch * p->dout[l] * 4) == cudaSuccess;
+    ok &= cudaMalloc(&p->dhb[l], (size_t)max_batch * p->dout[l] * 2) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    mdhp_init_model_destroy(p);
+    return init_fail(MDHP_E_NOMEM, "mdhp_init_model_create: allocation failed");
+  }
+  std::vector<int> mat(off / 256, 0);
+  for (int l = 0; l < 4; ++l)
+    for (int64_t e = p->off_w[l] / 256; e < (p->off_w[l] + (int64_t)p->din[l] * p->dout[l] + 255) / 256; ++e)
+      mat[e] = 1;
+  cudaMemcpy(p->is_matrix, mat.data(), mat.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemset(p->w, 0, off * 4);
+  cudaMemset(p->wb, 0, off * 2);
+  cudaMemset(p->m, 0, off * 4);
+  cudaMemset(p->v, 0, off * 4);
+  for (int l = 0; l < 4; ++l) {  // U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases
+    const int64_t n = (int64_t)p->din[l] * p->dout[l];
+    k_init_uniform<<<grid1(n), 256>>>(p->w + p->off_w[l], p->wb + p->off_w[l], n,
+                                      1.f / sqrtf((float)p->din[l]), seed, (uint64_t)l);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    mdhp_init_model_destroy(p);
+    return init_fail(MDHP_E_CUDA, "mdhp_init_model_create: initialisation failed");
+  }
+  *out = p;
+  return MDHP_OK;
+}
+
+void mdhp_init_model_destroy(mdhp_init_model *p) {
+  if (!p) return;
+  cudaFree(p->w); cudaFree(p->g); cudaFree(p->m); cudaFree(p->v); cudaFree(p->wb);
+  cudaFree(p->is_matrix); cudaFree(p->X); cudaFree(p->aux); cudaFree(p->loss);
+  for (int l = 0; l < 4; ++l) {
+    cudaFree(p->h[l]); cudaFree(p->hb[l]); cudaFree(p->dh[l]); cudaFree(p->dhb[l]);
+  }
+  delete p;
+}
+
+mdhp_status mdhp_init_model_info(const mdhp_init_model *p, int32_t *feature_dim, int32_t *out_dim,
+                                 int64_t *num_params, float **params_device) {
+  if (!p) return init_fail(MDHP_E_ARG, "mdhp_init_model_info: model NULL");
+  if (feature_dim) *feature_dim = p->K0;
+  if (out_dim) *out_dim = p->O;
+  if (num_params) *num_params = p->nparams;
+  if (params_device) *params_device = p->w;
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_init_model_sync_params(mdhp_init_model *p, void *stream) {
+  if (!p) return init_fail(MDHP_E_ARG, "mdhp_init_model_sync_params: model NULL");
+  // refresh the BF16 copy after the FP32 parameters were written by the caller
+  k_f32_to_bf16<<<grid1(p->nparams), 256, 0, (cudaStream_t)stream>>>(p->w, p->wb, p->nparams);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_init_features(const mdhp_batch *batch, const float *beta, void *features_bf16,
+                               float *mu_cold, void *stream) {
+  if (!batch || !beta || !features_bf16 || !mu_cold)
+    return init_fail(MDHP_E_ARG, "mdhp_init_features: NULL argument");
+  if (batch->M < 1 || batch->M > 32) return init_fail(MDHP_E_ARG, "mdhp_init_features: M must be 1..32");
+  if (batch->B <= 0) return MDHP_OK;
+  const int M = batch->M, Mt = M <= 4 ? 4 : M <= 8 ? 8 : M <= 16 ? 16 : 32;
+  const int K0 = init_k0(M);
+  const int nt = 128;
+  const int smem = (Mt * Mt * kBins + nt * Mt + Mt) * 4;
+  const int bstride = batch->beta_mode == MDHP_BETA_SCALAR ? 1 : M;
+  cudaStream_t st = (cudaStream_t)stream;
+#define MDHP_FEAT(MV)                                                                             \
+  case MV:                                                                                        \
+    if (smem > 48 * 1024)                                                                         \
+      cudaFuncSetAttribute(k_features<MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);    \
+    k_features<MV><<<batch->B, nt, smem, st>>>(batch->offsets, batch->t, batch->id,               \
+                                               batch->T_span, beta, bstride, M, K0,               \
+                                               (__nv_bfloat16 *)features_bf16, mu_cold);          \
+    break;
+  switch (Mt) {
+    MDHP_FEAT(4)
+    MDHP_FEAT(8)
+    MDHP_FEAT(16)
+    MDHP_FEAT(32)
+  }
+#undef MDHP_FEAT
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
+  return MDHP_OK;
+}
+
+// Forward over rows [0, Bn) of X (BF16 [Bn][K0]); leaves Y in h[3] (FP32).
+static void init_forward(mdhp_init_model *p, const __nv_bfloat16 *X, int Bn, cudaStream_t st) {
+  const __nv_bfloat16 *in = X;
+  for (int l = 0; l < 4; ++l) {
+    const int din = p->din[l], dout = p->dout[l];
+    launch_gemm(in, din, 1, p->wb + p->off_w[l], 1, din, Bn, dout, din, p->w + p->off_b[l],
+                l < 3 ? 1 : 0, p->h[l], p->hb[l], dout, 0, st);
+    in = p->hb[l];
+  }
+}
+
+mdhp_status mdhp_init_forward(mdhp_init_model *p, const void *features_bf16, int32_t B, float *out,
+                              void *stream) {
+  if (!p || !features_bf16 || !out) return init_fail(MDHP_E_ARG, "mdhp_init_forward: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int b0 = 0; b0 < B; b0 += p->max_batch) {
+    const int n = B - b0 < p->max_batch ? B - b0 : p->max_batch;
+    init_forward(p, (const __nv_bfloat16 *)features_bf16 + (size_t)b0 * p->K0, n, st);
+    cudaMemcpyAsync(out + (size_t)b0 * p->O, p->h[3], (size_t)n * p->O * 4, cudaMemcpyDeviceToDevice, st);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_init_predict(mdhp_init_model *p, const mdhp_batch *batch, const float *beta,
+                              float *mu, float *alpha, void *stream) {
+  if (!p || !batch || !beta || !mu || !alpha) return init_fail(MDHP_E_ARG, "mdhp_init_predict: NULL argument");
+  if (batch->M != p->M) return init_fail(MDHP_E_ARG, "mdhp_init_predict: batch M differs from the model's");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int bstride = batch->beta_mode == MDHP_BETA_SCALAR ? 1 : batch->M;
+  for (int b0 = 0; b0 < batch->B; b0 += p->max_batch) {
+    const int n = batch->B - b0 < p->max_batch ? batch->B - b0 : p->max_batch;
+    mdhp_batch sub = *batch;
+    sub.B = n;
+    sub.offsets = batch->offsets + b0;
+    sub.T_span = batch->T_span + b0;
+    const float *bsub = beta + (int64_t)b0 * bstride;
+    mdhp_status s = mdhp_init_features(&sub, bsub, p->X, p->aux, stream);
+    if (s != MDHP_OK) return s;
+    init_forward(p, p->X, n, st);
+    k_init_head<<<n, 128, 0, st>>>(p->h[3], p->O, p->aux, bsub, bstride, p->M, n,
+                                   mu + (int64_t)b0 * p->M, alpha + (int64_t)b0 * p->M * p->M);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_init_train_step(mdhp_init_model *p, const void *features_bf16,
+                                 const float *mu_cold, const float *beta, int32_t beta_stride,
+                                 const float *mu_target, const float *alpha_target, int32_t B,
+                                 float lr, float weight_decay, float *loss_out, void *stream) {
+  if (!p || !features_bf16 || !mu_cold || !beta || !mu_target || !alpha_target)
+    return init_fail(MDHP_E_ARG, "mdhp_init_train_step: NULL argument");
+  if (B < 1 || B > p->max_batch) return init_fail(MDHP_E_ARG, "mdhp_init_train_step: B outside 1..max_batch");
+  if (beta_stride != 1 && beta_stride != p->M) return init_fail(MDHP_E_ARG, "mdhp_init_train_step: beta_stride");
+  cudaStream_t st = (cudaStream_t)stream;
+  const __nv_bfloat16 *X = (const __nv_bfloat16 *)features_bf16;
+  init_forward(p, X, B, st);
+  cudaMemsetAsync(p->loss, 0, 4, st);
+  cudaMemsetAsync(p->g, 0, p->nparams * 4, st);
+  k_init_loss<<<B, 128, 0, st>>>(p->h[3], p->O, mu_cold, beta, beta_stride, p->M, B, mu_target,
+                                 alpha_target, p->dh[3], p->dhb[3], p->loss);
+  for (int l = 3; l >= 0; --l) {
+    const int din = p->din[l], dout = p->dout[l];
+    const __nv_bfloat16 *in = l > 0 ? p->hb[l - 1] : X;
+    // dW[dout][din] = dY^T [dout][B] x In [B][din]
+    launch_gemm(p->dhb[l], 1, dout, in, din, 1, dout, din, B, nullptr, 0, p->g + p->off_w[l], nullptr,
+                din, 1, st);
+    k_bias_grad<<<grid1(dout), 256, 0, st>>>(p->dh[l], B, dout, p->g + p->off_b[l]);
+    if (l > 0) {
+      // dIn[B][din] = dY [B][dout] x W [dout][din]; then the ReLU of layer l-1
+      launch_gemm(p->dhb[l], dout, 1, p->wb + p->off_w[l], din, 1, B, din, dout, nullptr, 0,
+                  p->dh[l - 1], nullptr, din, 0, st);
+      const int64_t n = (int64_t)B * din;
+      k_relu_bwd<<<grid1(n), 256, 0, st>>>(p->dh[l - 1], p->h[l - 1], p->dhb[l - 1], n);
+    }
+  }
+  p->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)p->step), c2 = 1.f - powf(b2, (float)p->step);
+  k_adamw<<<grid1(p->nparams), 256, 0, st>>>(p->w, p->g, p->m, p->v, p->wb, p->is_matrix,
+                                              p->nparams, lr, b1, b2, 1e-8f, weight_decay, c1, c2);
+  if (loss_out) cudaMemcpyAsync(loss_out, p->loss, 4, cudaMemcpyDeviceToDevice, st);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
+  return MDHP_OK;
+}
+
+}  // extern "C"
