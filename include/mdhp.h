@@ -213,7 +213,8 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
  * mu_cold [B][M] receives the fit's cold start 0.5 max(N_i, 1) / T.
  * Head: mu_i = mu_cold_i exp(clamp(y_i, -6, 6)), alpha_ij = beta_ij / M * softplus(y_ij).
  * Training loss per window (mean over the batch):
- *   sum_i (y_i - log(mu*_i / mu_cold_i))^2 + sum_ij (softplus(y_ij) - alpha*_ij M / beta_ij)^2.
+ *   sum_i (y_i - clamp(log(mu*_i / mu_cold_i), -6, 6))^2 + sum_ij (softplus(y_ij) - alpha*_ij M / beta_ij)^2
+ * (the clamp matches the head's range: a mu* at its floor is not chased to -inf).
  * M is limited to 1..32.
  */
 typedef struct mdhp_init_model mdhp_init_model;
@@ -225,12 +226,20 @@ mdhp_status mdhp_init_model_create(mdhp_init_model **model, int32_t M, int32_t h
                                    int32_t max_batch, uint64_t seed);
 void mdhp_init_model_destroy(mdhp_init_model *model);
 
-/* Sizes, and the device address of the flat FP32 parameter vector (layer l:
- * W_l [out][in] row-major then b_l [out], each block 256-aligned); after
- * writing it (checkpoint load) call mdhp_init_model_sync_params. */
+/* Sizes: feature_dim (padded), out_dim = M + M^2, num_params (the flat FP32
+ * parameter vector: layer l's W_l [out][in] row-major then b_l [out], each
+ * block starting at a multiple of 256 floats). */
 mdhp_status mdhp_init_model_info(const mdhp_init_model *model, int32_t *feature_dim,
-                                 int32_t *out_dim, int64_t *num_params, float **params_device);
-mdhp_status mdhp_init_model_sync_params(mdhp_init_model *model, void *stream);
+                                 int32_t *out_dim, int64_t *num_params);
+
+/* Copy the FP32 parameters (what = 0) or the gradient of the last
+ * mdhp_init_train_step (what = 1) into dst [num_params] (device). */
+mdhp_status mdhp_init_model_get(const mdhp_init_model *model, int32_t what, float *dst,
+                                void *stream);
+
+/* Replace the parameters from src [num_params] (device) and refresh the BF16
+ * copy (checkpoint load). */
+mdhp_status mdhp_init_model_set_params(mdhp_init_model *model, const float *src, void *stream);
 
 /* Features of every window of `batch` (beta per batch->beta_mode). */
 mdhp_status mdhp_init_features(const mdhp_batch *batch, const float *beta, void *features_bf16,

@@ -51,6 +51,18 @@ SIGNATURES = [
     ("mdhp_plan_set_path", ctypes.c_int, [P, ctypes.c_int32]),
     ("mdhp_fit_batch_noalloc", ctypes.c_int, [ctypes.POINTER(MdhpBatch), ctypes.POINTER(MdhpFitOpts),
                                               P, P, P, P, P, P, P]),
+    ("mdhp_init_model_create", ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_uint64]),
+    ("mdhp_init_model_destroy", None, [P]),
+    ("mdhp_init_model_info", ctypes.c_int, [P, P, P, P]),
+    ("mdhp_init_model_get", ctypes.c_int, [P, ctypes.c_int32, P, P]),
+    ("mdhp_init_model_set_params", ctypes.c_int, [P, P, P]),
+    ("mdhp_init_features", ctypes.c_int, [ctypes.POINTER(MdhpBatch), P, P, P, P]),
+    ("mdhp_init_forward", ctypes.c_int, [P, P, ctypes.c_int32, P, P]),
+    ("mdhp_init_predict", ctypes.c_int, [P, ctypes.POINTER(MdhpBatch), P, P, P, P]),
+    ("mdhp_init_train_step", ctypes.c_int, [P, P, P, P, ctypes.c_int32, P, P, ctypes.c_int32,
+                                            ctypes.c_float, ctypes.c_float, P, P]),
+    ("mdhp_plan_set_init_model", ctypes.c_int, [P, P]),
     ("mdhp_last_error", ctypes.c_char_p, []),
     ("mdhp_version", ctypes.c_int32, []),
 ]

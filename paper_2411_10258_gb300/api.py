@@ -221,3 +221,87 @@ class LoglikGrad(torch.autograd.Function):
             counts = offsets[1:] - offsets[:-1]
             d_w = g_w * torch.repeat_interleave(go, counts)
         return None, d_mu, d_alpha, d_beta, d_w
+
+
+class InitModel:
+    """Learned warm start (mdhp_init_model): features -> 4-layer BF16 MLP -> (mu, alpha).
+
+    Training runs on the GPU through mdhp_init_train_step; this class only
+    allocates the torch buffers the C ABI writes into."""
+
+    def __init__(self, M: int, hidden: int = 256, max_batch: int = 256, seed: int = 1024):
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.mdhp_init_model_create(ctypes.byref(h), M, hidden, max_batch, seed),
+                   "mdhp_init_model_create")
+        self.h = h
+        self.M, self.hidden, self.max_batch = M, hidden, max_batch
+        fd, od, npar = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _lib.check(self.lib.mdhp_init_model_info(self.h, ctypes.byref(fd), ctypes.byref(od),
+                                                 ctypes.byref(npar)), "mdhp_init_model_info")
+        self.feature_dim, self.out_dim, self.num_params = fd.value, od.value, npar.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mdhp_init_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self, what: str = "params", stream=None) -> torch.Tensor:
+        out = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        _lib.check(self.lib.mdhp_init_model_get(self.h, 0 if what == "params" else 1, _ptr(out),
+                                                _stream(stream)), "mdhp_init_model_get")
+        return out
+
+    def set_params(self, params: torch.Tensor, stream=None):
+        params = params.contiguous().float().cuda()
+        assert params.numel() == self.num_params
+        _lib.check(self.lib.mdhp_init_model_set_params(self.h, _ptr(params), _stream(stream)),
+                   "mdhp_init_model_set_params")
+
+    def features(self, db: DeviceBatch, beta: torch.Tensor, stream=None):
+        """(features bfloat16 [B, feature_dim], mu_cold float32 [B, M])."""
+        feat = torch.empty(db.B, self.feature_dim, dtype=torch.bfloat16, device=db.t.device)
+        mu_cold = torch.empty(db.B, db.M, dtype=torch.float32, device=db.t.device)
+        st = db.c_struct()
+        beta = beta.contiguous().float()
+        _lib.check(self.lib.mdhp_init_features(ctypes.byref(st), _ptr(beta), _ptr(feat),
+                                               _ptr(mu_cold), _stream(stream)), "mdhp_init_features")
+        return feat, mu_cold
+
+    def forward(self, feat: torch.Tensor, stream=None) -> torch.Tensor:
+        out = torch.empty(feat.shape[0], self.out_dim, dtype=torch.float32, device=feat.device)
+        _lib.check(self.lib.mdhp_init_forward(self.h, _ptr(feat.contiguous()), feat.shape[0],
+                                              _ptr(out), _stream(stream)), "mdhp_init_forward")
+        return out
+
+    def predict(self, db: DeviceBatch, beta: torch.Tensor, stream=None):
+        mu = torch.empty(db.B, db.M, dtype=torch.float32, device=db.t.device)
+        alpha = torch.empty(db.B, db.M, db.M, dtype=torch.float32, device=db.t.device)
+        st = db.c_struct()
+        _lib.check(self.lib.mdhp_init_predict(self.h, ctypes.byref(st), _ptr(beta.contiguous().float()),
+                                              _ptr(mu), _ptr(alpha), _stream(stream)),
+                   "mdhp_init_predict")
+        return mu, alpha
+
+    def train_step(self, feat, mu_cold, beta, mu_target, alpha_target, lr=3e-4, weight_decay=5e-5,
+                   loss_out: torch.Tensor | None = None, stream=None):
+        B = feat.shape[0]
+        beta = beta.contiguous().float()
+        bstride = 1 if beta.numel() == B else self.M
+        if loss_out is None:
+            loss_out = torch.empty(1, dtype=torch.float32, device=feat.device)
+        _lib.check(self.lib.mdhp_init_train_step(
+            self.h, _ptr(feat.contiguous()), _ptr(mu_cold.contiguous()), _ptr(beta), bstride,
+            _ptr(mu_target.contiguous().float()), _ptr(alpha_target.contiguous().float()), B,
+            float(lr), float(weight_decay), _ptr(loss_out), _stream(stream)), "mdhp_init_train_step")
+        return loss_out
+
+    def attach(self, plan: "Plan"):
+        """Use this model for FitOptions(init=2) fits of `plan`."""
+        _lib.check(self.lib.mdhp_plan_set_init_model(plan.h, self.h), "mdhp_plan_set_init_model")

@@ -15,7 +15,7 @@
 // Network: X [B, K0] -> 4 layers (ReLU between) -> Y [B, M + M^2].
 // Head:    mu_i = mu_cold_i exp(clamp(y_i, -6, 6)), alpha_ij = (beta / M) softplus(y_ij),
 //          mu_cold the fit's cold start 0.5 max(N_i, 1) / T.
-// Loss (training, per window): sum_i (y_i - log(mu*_i / mu_cold_i))^2 +
+// Loss (training, per window): sum_i (y_i - clamp(log(mu*_i / mu_cold_i), -6, 6))^2 +
 //          sum_ij (softplus(y_ij) - alpha*_ij M / beta)^2, averaged over windows.
 #include <cuda_bf16.h>
 
@@ -283,7 +283,8 @@ __global__ void k_init_loss(const float *Y, int O, const float *aux, const float
     float d = 0.f;
     const float y = Y[(size_t)b * O + p];
     if (p < Mrt) {
-      const float z = logf(fmaxf(mu_t[(int64_t)b * Mrt + p], 1e-20f) / aux[(int64_t)b * Mrt + p]);
+      const float z = fminf(fmaxf(logf(fmaxf(mu_t[(int64_t)b * Mrt + p], 1e-20f) / aux[(int64_t)b * Mrt + p]),
+                                  -6.f), 6.f);
       const float e = y - z;
       acc += e * e;
       d = 2.f * e * inv;
@@ -480,19 +481,28 @@ void mdhp_init_model_destroy(mdhp_init_model *p) {
 }
 
 mdhp_status mdhp_init_model_info(const mdhp_init_model *p, int32_t *feature_dim, int32_t *out_dim,
-                                 int64_t *num_params, float **params_device) {
+                                 int64_t *num_params) {
   if (!p) return init_fail(MDHP_E_ARG, "mdhp_init_model_info: model NULL");
   if (feature_dim) *feature_dim = p->K0;
   if (out_dim) *out_dim = p->O;
   if (num_params) *num_params = p->nparams;
-  if (params_device) *params_device = p->w;
   return MDHP_OK;
 }
 
-mdhp_status mdhp_init_model_sync_params(mdhp_init_model *p, void *stream) {
-  if (!p) return init_fail(MDHP_E_ARG, "mdhp_init_model_sync_params: model NULL");
-  // refresh the BF16 copy after the FP32 parameters were written by the caller
-  k_f32_to_bf16<<<grid1(p->nparams), 256, 0, (cudaStream_t)stream>>>(p->w, p->wb, p->nparams);
+mdhp_status mdhp_init_model_get(const mdhp_init_model *p, int32_t what, float *dst, void *stream) {
+  if (!p || !dst || (what != 0 && what != 1)) return init_fail(MDHP_E_ARG, "mdhp_init_model_get: bad argument");
+  if (cudaMemcpyAsync(dst, what == 0 ? p->w : p->g, p->nparams * 4, cudaMemcpyDeviceToDevice,
+                      (cudaStream_t)stream) != cudaSuccess)
+    return init_fail(MDHP_E_CUDA, cudaGetErrorString(cudaGetLastError()));
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_init_model_set_params(mdhp_init_model *p, const float *src, void *stream) {
+  if (!p || !src) return init_fail(MDHP_E_ARG, "mdhp_init_model_set_params: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(p->w, src, p->nparams * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return init_fail(MDHP_E_CUDA, cudaGetErrorString(cudaGetLastError()));
+  k_f32_to_bf16<<<grid1(p->nparams), 256, 0, st>>>(p->w, p->wb, p->nparams);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
   return MDHP_OK;
