@@ -421,7 +421,7 @@ mdhp_status mdhp_plan_get_shape(const mdhp_plan *p, int32_t *nt, int32_t *spl, i
 
 mdhp_status mdhp_plan_set_shape(mdhp_plan *p, int32_t nt, int32_t spl, int32_t cutoff) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
-  if (nt < 32 || nt > 512 || nt % 32 != 0) return fail(MDHP_E_ARG, "threads per window %d", nt);
+  if (nt < 32 || nt > 256 || nt % 32 != 0) return fail(MDHP_E_ARG, "threads per window %d (32..256, multiple of 32)", nt);
   if (nt < p->Mt) return fail(MDHP_E_ARG, "threads per window must be >= %d", p->Mt);
   if (!get_fit(p->Mt, spl, p->beta_mode, false, true))
     return fail(MDHP_E_UNSUPPORTED, "threads per chunk %d not built for M<=%d", spl, p->Mt);
