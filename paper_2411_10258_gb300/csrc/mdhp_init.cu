@@ -156,6 +156,7 @@ struct GemmArgs {
   int Mm, Nn, Kk;
   const float *bias;
   int relu, accumulate;
+  int vec_a, vec_b;  // k contiguous and 8-aligned: vectorised tile loads
   float *Cf;
   __nv_bfloat16 *Cb;
   int64_t ldc;
@@ -186,16 +187,38 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
   const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  // 16-byte loads when k is the contiguous dimension (8 bf16 per load); the
+  // host only sets vec_* when strides and sizes are multiples of 8
   for (int k0 = 0; k0 < g.Kk; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += 128) {
-      const int r = e / BK, kk = e % BK;
-      const int m = m0 + r, k = k0 + kk;
-      As[r][kk] = (m < g.Mm && k < g.Kk) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : zero;
+    if (g.vec_a) {
+      for (int e = tid; e < BM * BK / 8; e += 128) {
+        const int r = e / (BK / 8), kk = (e % (BK / 8)) * 8;
+        const int m = m0 + r, k = k0 + kk;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (m < g.Mm && k < g.Kk) v = *reinterpret_cast<const uint4 *>(g.A + (int64_t)m * g.sam + k);
+        *reinterpret_cast<uint4 *>(&As[r][kk]) = v;
+      }
+    } else {
+      for (int e = tid; e < BM * BK; e += 128) {
+        const int r = e / BK, kk = e % BK;
+        const int m = m0 + r, k = k0 + kk;
+        As[r][kk] = (m < g.Mm && k < g.Kk) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : zero;
+      }
     }
-    for (int e = tid; e < BN * BK; e += 128) {
-      const int r = e / BK, kk = e % BK;
-      const int n = n0 + r, k = k0 + kk;
-      Bs[r][kk] = (n < g.Nn && k < g.Kk) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : zero;
+    if (g.vec_b) {
+      for (int e = tid; e < BN * BK / 8; e += 128) {
+        const int r = e / (BK / 8), kk = (e % (BK / 8)) * 8;
+        const int n = n0 + r, k = k0 + kk;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (n < g.Nn && k < g.Kk) v = *reinterpret_cast<const uint4 *>(g.B + (int64_t)n * g.sbn + k);
+        *reinterpret_cast<uint4 *>(&Bs[r][kk]) = v;
+      }
+    } else {
+      for (int e = tid; e < BN * BK; e += 128) {
+        const int r = e / BK, kk = e % BK;
+        const int n = n0 + r, k = k0 + kk;
+        Bs[r][kk] = (n < g.Nn && k < g.Kk) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : zero;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -391,7 +414,9 @@ static void launch_gemm(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const 
                         int64_t sbk, int64_t sbn, int Mm, int Nn, int Kk, const float *bias,
                         int relu, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, int accumulate,
                         cudaStream_t st) {
-  GemmArgs g{A, B, sam, sak, sbk, sbn, Mm, Nn, Kk, bias, relu, accumulate, Cf, Cb, ldc};
+  const int va = (sak == 1 && sam % 8 == 0 && Kk % 8 == 0 && ((uintptr_t)A & 15) == 0) ? 1 : 0;
+  const int vb = (sbk == 1 && sbn % 8 == 0 && Kk % 8 == 0 && ((uintptr_t)B & 15) == 0) ? 1 : 0;
+  GemmArgs g{A, B, sam, sak, sbk, sbn, Mm, Nn, Kk, bias, relu, accumulate, va, vb, Cf, Cb, ldc};
   dim3 grid((Nn + 63) / 64, (Mm + 63) / 64);
   k_gemm_bf16<<<grid, 128, 0, st>>>(g);
 }
