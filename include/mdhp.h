@@ -53,7 +53,9 @@ typedef enum {
   MDHP_E_TIMEOUT = 7,      /* reserved: a bounded device-side wait gave up */
   MDHP_E_CUDA = 8,         /* a CUDA call failed */
   MDHP_E_NOMEM = 9,        /* plan allocation failed */
-  MDHP_E_UNSUPPORTED = 10  /* valid request this build does not implement */
+  MDHP_E_UNSUPPORTED = 10, /* valid request this build does not implement */
+  MDHP_E_SIM_STALLED = 11  /* mdhp_simulate: the intensity vanished (or the candidate
+                              limit was hit) before the window had its events */
 } mdhp_status;
 
 typedef enum {
@@ -304,6 +306,45 @@ mdhp_status mdhp_plan_set_path(mdhp_plan *plan, int32_t path);
 mdhp_status mdhp_fit_batch_noalloc(const mdhp_batch *batch, const mdhp_fit_opts *opts, float *mu,
                                    float *alpha, float *beta, double *loglik, int32_t *iters,
                                    int32_t *win_status, void *stream);
+
+/*
+ * Bulk simulation of windows of the exponential-kernel MDHP (the intensity of
+ * Sec. II, with beta scalar or per source) by Ogata's thinning (Ogata 1981)
+ * on the GPU, one thread per window in FP64.  Produces training windows for
+ * the learned initializer and test data; an addition of this library (the
+ * paper's windows are recorded traffic).
+ *   M, beta_mode   1..64; MDHP_BETA_SCALAR or MDHP_BETA_PER_SOURCE (matrix:
+ *                  MDHP_E_UNSUPPORTED).
+ *   mu       double[B][M]     baseline rates (>= 0, finite)
+ *   alpha    double[B][M][M]  row = target, column = source (>= 0, finite)
+ *   beta     double[B][nb]    decays (> 0, finite), nb = 1 or M
+ *   offsets  int64[B+1]       CSR output layout; window b gets exactly
+ *                             N_b = offsets[b+1] - offsets[b] events
+ *   order    int32[B] or NULL a permutation of 0..B-1: thread r simulates
+ *                             window order[r] (longest first keeps a warp's
+ *                             lanes busy for similar times); NULL = identity
+ *   seed, stream_id, first_window
+ *                             window b draws from the SplitMix64 counter
+ *                             stream keyed by (seed, stream_id, first_window + b)
+ *                             (Steele, Lea, Flood 2014), so its events do not
+ *                             depend on the launch or on the other windows
+ *   t        float[offsets[B]]  out: event times (seconds from window start,
+ *                             non-decreasing; FP64 simulation rounded to float)
+ *   id       int16[offsets[B]]  out: event types
+ *   T_span   float[B]         out: the time of the (N_b + 1)-th accepted point,
+ *                             which closes the window (never below its last event)
+ *   win_status int32[B]       out: MDHP_OK, MDHP_E_ARG (bad parameters or
+ *                             offsets; nothing written but T_span = 0) or
+ *                             MDHP_E_SIM_STALLED (events written so far kept)
+ * The same (seed, stream_id, window index) gives the events of the CPU
+ * generator with the same definition, up to the rounding of exp/log1p and of
+ * the sums.  Asynchronous on `stream`; no allocation.
+ */
+mdhp_status mdhp_simulate(int32_t M, int32_t beta_mode, int32_t B, const double *mu,
+                          const double *alpha, const double *beta, const int64_t *offsets,
+                          const int32_t *order, uint64_t seed, uint64_t stream_id,
+                          uint64_t first_window, float *t, int16_t *id, float *T_span,
+                          int32_t *win_status, void *stream);
 
 /* Text of the last error in this thread (static storage). */
 const char *mdhp_last_error(void);

@@ -13,9 +13,10 @@ LIBPATH = os.path.join(_HERE, "_build", "libmdhp.so")
 NOALLOC_MAX_WINDOWS = 65536  # MDHP_NOALLOC_MAX_WINDOWS in include/mdhp.h
 
 OK, E_ARG, E_UNSORTED, E_ID_RANGE, E_TIME_RANGE, E_NONFINITE, E_MAXITER, E_TIMEOUT, E_CUDA, \
-    E_NOMEM, E_UNSUPPORTED = range(11)
+    E_NOMEM, E_UNSUPPORTED, E_SIM_STALLED = range(12)
 STATUS_NAMES = ["OK", "E_ARG", "E_UNSORTED", "E_ID_RANGE", "E_TIME_RANGE", "E_NONFINITE",
-                "E_MAXITER", "E_TIMEOUT", "E_CUDA", "E_NOMEM", "E_UNSUPPORTED"]
+                "E_MAXITER", "E_TIMEOUT", "E_CUDA", "E_NOMEM", "E_UNSUPPORTED",
+                "E_SIM_STALLED"]
 
 P = ctypes.c_void_p
 
@@ -51,6 +52,8 @@ SIGNATURES = [
     ("mdhp_plan_set_path", ctypes.c_int, [P, ctypes.c_int32]),
     ("mdhp_fit_batch_noalloc", ctypes.c_int, [ctypes.POINTER(MdhpBatch), ctypes.POINTER(MdhpFitOpts),
                                               P, P, P, P, P, P, P]),
+    ("mdhp_simulate", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P,
+                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P, P]),
     ("mdhp_init_model_create", ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_uint64]),
     ("mdhp_init_model_destroy", None, [P]),

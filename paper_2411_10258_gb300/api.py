@@ -24,7 +24,7 @@ def _stream(stream=None):
 
 
 def nbeta(beta_mode: int, M: int) -> int:
-    return 1 if beta_mode == 0 else M
+    return 1 if beta_mode == 0 else (M if beta_mode == 1 else M * M)
 
 
 @dataclass
@@ -93,6 +93,42 @@ def loglik_grad(db: DeviceBatch, mu: torch.Tensor, alpha: torch.Tensor, beta: to
     _lib.check(rc, "mdhp_loglik_grad")
     out["_keep"] = (r_work, mu, alpha, beta)
     return out
+
+
+def simulate(M: int, beta_mode: int, mu, alpha, beta, counts, seed: int, stream_id: int,
+             first_window: int = 0, device="cuda", stream=None):
+    """Simulate windows with exactly counts[b] events each on the GPU
+    (mdhp_simulate, Ogata thinning in FP64).  mu [B,M], alpha [B,M,M] and beta
+    [B,nb] are float64 (host arrays or device tensors); counts is a host int
+    array.  Windows run longest first.  Returns (DeviceBatch, status int32[B])."""
+    lib = _lib.load()
+    dev = torch.device(device)
+    counts = np.asarray(counts, dtype=np.int64)
+    B = len(counts)
+    offsets = np.zeros(B + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    order = np.argsort(-counts, kind="stable").astype(np.int32)
+
+    def dev64(x, shape):
+        x = torch.as_tensor(x, dtype=torch.float64, device=dev)
+        return x.reshape(shape).contiguous()
+
+    mu = dev64(mu, (B, M))
+    alpha = dev64(alpha, (B, M, M))
+    beta = dev64(beta, (B, nbeta(beta_mode, M)))
+    n = int(offsets[-1])
+    off_d = torch.from_numpy(offsets).to(dev)
+    order_d = torch.from_numpy(order).to(dev)
+    t = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
+    ids = torch.empty(max(n, 1), dtype=torch.int16, device=dev)
+    T = torch.empty(B, dtype=torch.float32, device=dev)
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    _lib.check(lib.mdhp_simulate(M, beta_mode, B, _ptr(mu), _ptr(alpha), _ptr(beta), _ptr(off_d),
+                                 _ptr(order_d), int(seed), int(stream_id), int(first_window),
+                                 _ptr(t), _ptr(ids), _ptr(T), _ptr(status), _stream(stream)),
+               "mdhp_simulate")
+    me = int(counts.max()) if B else 0
+    return DeviceBatch(M, beta_mode, off_d, t[:n], ids[:n], T, None, me), status
 
 
 @dataclass
