@@ -226,23 +226,12 @@ def log_uniform_counts(rng, B, lo, hi):
     return np.round(np.exp(rng.uniform(np.log(lo), np.log(hi), size=B))).astype(np.int64)
 
 
-def make_workload(name: int, B: int | None = None, seed: int = BASE_SEED, beta: float = 1.0,
-                  nthreads: int = 0) -> Batch:
-    """Build one of the five workloads (see module docstring); B overrides the
-    window count (the shapes and distributions stay those of the workload)."""
+def make_params(name: int, B: int | None = None, seed: int = BASE_SEED, beta: float = 1.0) -> dict:
+    """Parameters and event counts of workload 2..5 (see module docstring) without
+    simulating: dict(M, mode, mu, alpha, beta, counts, meta).  Feeds the CPU
+    generator here and the library's GPU simulator alike."""
     rng = np.random.default_rng([seed, name])
-    if name == 1:
-        M, mode = 4, 0
-        mu = rng.uniform(0.1, 1.0, size=(1, M))
-        alpha = rng.uniform(0.0, 1.0, size=(1, M, M))
-        alpha *= 0.5 / spectral_radius(alpha / 1.0)[:, None, None]
-        G = alpha[0] / 1.0
-        rate = np.linalg.solve(np.eye(M) - G, mu[0]).sum()
-        c = 2000.0 / (100.0 * rate)
-        mu *= c
-        bt = simulate_fixed_T(M, mode, mu[0], alpha[0], np.array([1.0]), 100.0, seed, name)
-        bt.meta.update(name=1, mu_scale=float(c))
-        return bt
+    meta = dict(name=name)
     if name == 2:
         B = 4096 if B is None else B
         M, mode = 16, 0
@@ -272,10 +261,30 @@ def make_workload(name: int, B: int | None = None, seed: int = BASE_SEED, beta: 
         mu, alpha = sample_params(rng, B, M, mode, betas, rho)
         injected, ks = inject_component(rng, mu, alpha, betas, mode, M, 0.10)
         counts = log_uniform_counts(rng, B, 100, 10000)
+        meta.update(injected=injected, injected_k=ks)
     else:
         raise ValueError(f"unknown workload {name}")
-    bt = simulate(M, mode, mu, alpha, betas, counts, seed, name, nthreads)
-    bt.meta.update(name=name)
-    if name == 5:
-        bt.meta.update(injected=injected, injected_k=ks)
+    return dict(M=M, mode=mode, mu=mu, alpha=alpha, beta=betas, counts=counts, meta=meta)
+
+
+def make_workload(name: int, B: int | None = None, seed: int = BASE_SEED, beta: float = 1.0,
+                  nthreads: int = 0) -> Batch:
+    """Build one of the five workloads (see module docstring); B overrides the
+    window count (the shapes and distributions stay those of the workload)."""
+    if name == 1:
+        rng = np.random.default_rng([seed, name])
+        M, mode = 4, 0
+        mu = rng.uniform(0.1, 1.0, size=(1, M))
+        alpha = rng.uniform(0.0, 1.0, size=(1, M, M))
+        alpha *= 0.5 / spectral_radius(alpha / 1.0)[:, None, None]
+        G = alpha[0] / 1.0
+        rate = np.linalg.solve(np.eye(M) - G, mu[0]).sum()
+        c = 2000.0 / (100.0 * rate)
+        mu *= c
+        bt = simulate_fixed_T(M, mode, mu[0], alpha[0], np.array([1.0]), 100.0, seed, name)
+        bt.meta.update(name=1, mu_scale=float(c))
+        return bt
+    p = make_params(name, B, seed, beta)
+    bt = simulate(p["M"], p["mode"], p["mu"], p["alpha"], p["beta"], p["counts"], seed, name, nthreads)
+    bt.meta.update(p["meta"])
     return bt
