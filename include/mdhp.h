@@ -194,11 +194,39 @@ float mdhp_plan_last_fit_ms(mdhp_plan *plan);
  * threads per chunk of the event recursion, and the shared-memory cutoff:
  * windows of at most this many events are staged in shared memory (the
  * recursion) or keep their decoupled features in shared memory (fixed beta);
- * longer windows stream from device memory.  A cutoff of 0 streams all. */
+ * longer windows stream from device memory.  A cutoff of 0 streams all.
+ * When the plan has decoupled-feature scratch and the path is MDHP_PATH_AUTO,
+ * get_shape reports the decoupled kernels' threads per window and cutoff. */
 mdhp_status mdhp_plan_get_shape(const mdhp_plan *plan, int32_t *threads_per_window,
                                 int32_t *threads_per_chunk, int32_t *smem_cutoff_events);
 mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
                                 int32_t threads_per_chunk, int32_t smem_cutoff_events);
+
+/*
+ * Autotuner (an addition of this library): times mdhp_fit_batch on `batch`
+ * with `opts` for each candidate launch shape and keeps the fastest in the
+ * plan.  Candidates: 64, 128 and 256 threads per window; for the decoupled
+ * fixed-beta kernels the shared-memory class (none, half, the largest that
+ * fits); for the event recursion every built threads-per-chunk split and the
+ * staging cutoff (none, the default, the largest that fits).  Each candidate
+ * runs tune_iters iterations (<= 0: 20) with tol = 0 after one warm-up run.
+ *   mu, alpha, beta  device, as for mdhp_fit_batch; used as the starting point
+ *                    when opts->init == 0 and restored on return
+ *   loglik, iters, win_status  device scratch, overwritten
+ *   chosen   int32[4] host or NULL: path (0 decoupled, 1 recursion), threads
+ *            per window, threads per chunk (0 for decoupled), cutoff
+ *   best_ms  float host or NULL: device time of the chosen shape
+ * When the plan was created with an autotune_cache path, the choice is
+ * written there under a key of the device name and compute capability, M,
+ * beta_mode, max_windows and max_events_per_window and the kernel family;
+ * mdhp_plan_create with the same arguments and file applies it.
+ * Synchronises `stream`; allocates a temporary copy of mu/alpha/beta; not
+ * capturable in a CUDA graph (tune first, then capture).
+ */
+mdhp_status mdhp_plan_autotune(mdhp_plan *plan, const mdhp_batch *batch, const mdhp_fit_opts *opts,
+                               float *mu, float *alpha, float *beta, double *loglik, int32_t *iters,
+                               int32_t *win_status, int32_t tune_iters, int32_t *chosen,
+                               float *best_ms, void *stream);
 
 /*
  * Learned warm start (an addition of this library; the paper starts its

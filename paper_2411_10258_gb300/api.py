@@ -199,6 +199,30 @@ class Plan:
         _lib.check(self.lib.mdhp_plan_set_shape(self.h, threads_per_window, threads_per_chunk, cutoff),
                    "mdhp_plan_set_shape")
 
+    def autotune(self, db: DeviceBatch, opts: FitOptions, mu: torch.Tensor, alpha: torch.Tensor,
+                 beta: torch.Tensor, tune_iters: int = 20, stream=None) -> dict:
+        """mdhp_plan_autotune: time the candidate launch shapes on this batch and
+        keep the fastest (written to the plan's cache file, if any).  mu/alpha/beta
+        are restored on return.  Returns the choice and its device time."""
+        B = db.B
+        dev = db.t.device
+        for x in (mu, alpha, beta):
+            assert x.is_contiguous() and x.dtype == torch.float32 and x.device == dev
+        scratch = dict(loglik=torch.empty(B, dtype=torch.float64, device=dev),
+                       iters=torch.empty(B, dtype=torch.int32, device=dev),
+                       status=torch.empty(B, dtype=torch.int32, device=dev))
+        chosen = (ctypes.c_int32 * 4)()
+        best = ctypes.c_float(-1.0)
+        st = db.c_struct()
+        o = opts.c_struct()
+        rc = self.lib.mdhp_plan_autotune(self.h, ctypes.byref(st), ctypes.byref(o), _ptr(mu),
+                                         _ptr(alpha), _ptr(beta), _ptr(scratch["loglik"]),
+                                         _ptr(scratch["iters"]), _ptr(scratch["status"]),
+                                         int(tune_iters), chosen, ctypes.byref(best), _stream(stream))
+        _lib.check(rc, "mdhp_plan_autotune")
+        return dict(path=("decoupled", "recursion")[chosen[0]], threads_per_window=chosen[1],
+                    threads_per_chunk=chosen[2], cutoff=chosen[3], ms=best.value)
+
     def fit(self, db: DeviceBatch, opts: FitOptions, mu: torch.Tensor, alpha: torch.Tensor,
             beta: torch.Tensor, out: dict | None = None, stream=None) -> dict:
         """mdhp_fit_batch; mu/alpha/beta are updated in place (float32, contiguous)."""

@@ -6,6 +6,10 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
+#include <vector>
+
+#include <unistd.h>
 
 #include "mdhp.h"
 #include "mdhp_dispatch.h"
@@ -167,7 +171,158 @@ struct mdhp_plan {
   int xres_max = 0;          // largest shared-memory class the device allows
   int use_x = 1;  // 0 forces the recursion kernels (for tests and comparisons)
   mdhp_init_model *model = nullptr;  // learned initializer (not owned)
+  std::string cache;                 // autotune cache file ("" = none)
 };
+
+// --- autotuner: cache of tuned launch shapes ---------------------------------
+//
+// The cache is a small JSON file, one entry per line:
+//   {"format": "mdhp-autotune-1", "entries": [
+//   {"key": "<device>|sm<cc>|M<M>|mode<m>|W<max_windows>|E<max_events>|<path>",
+//    "threads_per_window": 64, "threads_per_chunk": 0, "smem_cutoff_events": 0, "ms": 14.8},
+//   ...]}
+// keyed by the device and the plan's creation arguments; <path> is "decoupled"
+// (fixed-beta features kernels: threads per window and the shared-memory
+// class) or "recursion" (threads per window, threads per chunk, staging cutoff).
+namespace mdhp {
+namespace {
+
+std::string tune_key(const mdhp_plan *p, int path) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  std::string name = prop.name;
+  for (char &c : name)
+    if (c == '"' || c == '\\' || c == '|' || (unsigned char)c < 32) c = '_';
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s|sm%d%d|M%d|mode%d|W%d|E%lld|%s", name.c_str(), prop.major,
+           prop.minor, p->M, p->beta_mode, p->max_windows, (long long)p->max_events,
+           path == 0 ? "decoupled" : "recursion");
+  return buf;
+}
+
+bool read_text(const std::string &path, std::string &out) {
+  FILE *f = fopen(path.c_str(), "rb");
+  if (!f) return false;
+  char buf[4096];
+  size_t n;
+  out.clear();
+  while ((n = fread(buf, 1, sizeof(buf), f)) > 0) out.append(buf, n);
+  fclose(f);
+  return true;
+}
+
+// (key, entry text) for every entry of a cache file
+std::vector<std::pair<std::string, std::string>> cache_entries(const std::string &text) {
+  std::vector<std::pair<std::string, std::string>> v;
+  const std::string open = "{\"key\": \"";
+  size_t pos = 0;
+  while ((pos = text.find(open, pos)) != std::string::npos) {
+    const size_t ks = pos + open.size();
+    const size_t ke = text.find('"', ks);
+    if (ke == std::string::npos) break;
+    const size_t le = text.find('}', ke);
+    if (le == std::string::npos) break;
+    v.emplace_back(text.substr(ks, ke - ks), text.substr(pos, le - pos + 1));
+    pos = le + 1;
+  }
+  return v;
+}
+
+int field_int(const std::string &entry, const char *name, int dflt) {
+  const std::string pat = std::string("\"") + name + "\": ";
+  const size_t p = entry.find(pat);
+  if (p == std::string::npos) return dflt;
+  return (int)strtol(entry.c_str() + p + pat.size(), nullptr, 10);
+}
+
+// largest events-per-window class of the decoupled kernels that fits the
+// shared memory of one CTA of nt threads (0 if none)
+int xres_fit(const mdhp_plan *p, int nt, bool adam) {
+  const int fixed = make_carve_x(p->Mt, nt, 0, adam).total;
+  int fit = ((max_dyn_smem() - 1024 - fixed) / (p->Mt * 4)) / 32 * 32;
+  if (fit > p->xcap) fit = p->xcap / 32 * 32;
+  return fit >= 64 ? fit : 0;
+}
+
+// largest staging capacity of the recursion kernels for (nt, spl) (0 if none)
+int stage_fit(const mdhp_plan *p, int nt, int spl, bool weights, bool learn, bool adam) {
+  int lo = 0, hi = 1 << 20;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (make_carve(p->Mt, nt, spl, mid, weights, learn, adam, true, use_priv(p->Mt)).total <=
+        max_dyn_smem())
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo / 32 * 32;
+}
+
+bool apply_decoupled(mdhp_plan *p, int nt, int xres) {
+  if (nt < 64 || nt > 256 || (nt & (nt - 1)) || nt < p->Mt) return false;
+  if (xres < 0 || (xres > 0 && (xres < 64 || xres > xres_fit(p, nt, false)))) return false;
+  p->xnt = nt;
+  p->xres = xres;
+  return true;
+}
+
+bool apply_recursion(mdhp_plan *p, int nt, int spl, int cutoff) {
+  if (nt < 32 || nt > 256 || nt % 32 || nt < p->Mt || spl < 1 || nt % spl || cutoff < 0) return false;
+  if (!get_fit(p->Mt, spl, p->beta_mode, false, true)) return false;
+  p->shape = Shape{nt, spl, cutoff};
+  return true;
+}
+
+void tune_load(mdhp_plan *p) {
+  std::string text;
+  if (!read_text(p->cache, text)) return;
+  const auto v = cache_entries(text);
+  for (int path = 0; path < 2; ++path) {
+    const std::string key = tune_key(p, path);
+    for (const auto &e : v) {
+      if (e.first != key) continue;
+      const int nt = field_int(e.second, "threads_per_window", 0);
+      const int spl = field_int(e.second, "threads_per_chunk", 0);
+      const int cut = field_int(e.second, "smem_cutoff_events", -1);
+      if (path == 0 && p->xbuf) apply_decoupled(p, nt, cut);
+      if (path == 1) apply_recursion(p, nt, spl, cut);
+    }
+  }
+  cudaGetLastError();
+}
+
+bool tune_store(const mdhp_plan *p, int path, int nt, int spl, int cutoff, float ms) {
+  if (p->cache.empty()) return true;
+  std::string text;
+  read_text(p->cache, text);
+  auto v = cache_entries(text);
+  const std::string key = tune_key(p, path);
+  char line[768];
+  snprintf(line, sizeof(line),
+           "{\"key\": \"%s\", \"threads_per_window\": %d, \"threads_per_chunk\": %d, "
+           "\"smem_cutoff_events\": %d, \"ms\": %.4f}",
+           key.c_str(), nt, spl, cutoff, ms);
+  bool found = false;
+  for (auto &e : v)
+    if (e.first == key) {
+      e.second = line;
+      found = true;
+    }
+  if (!found) v.emplace_back(key, line);
+  const std::string tmp = p->cache + ".tmp" + std::to_string((long)getpid());
+  FILE *f = fopen(tmp.c_str(), "wb");
+  if (!f) return false;
+  fprintf(f, "{\"format\": \"mdhp-autotune-1\", \"entries\": [\n");
+  for (size_t i = 0; i < v.size(); ++i) fprintf(f, "%s%s\n", v[i].second.c_str(), i + 1 < v.size() ? "," : "");
+  fprintf(f, "]}\n");
+  const bool ok = fclose(f) == 0;
+  return ok && rename(tmp.c_str(), p->cache.c_str()) == 0;
+}
+
+}  // namespace
+}  // namespace mdhp
 
 extern "C" {
 
@@ -276,7 +431,6 @@ __global__ void k_split(const int *keys_sorted, int B, int cutoff, int has_long,
 
 mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int32_t max_windows,
                              int64_t max_events_per_window, const char *autotune_cache) {
-  (void)autotune_cache;
   if (!out) return fail(MDHP_E_ARG, "plan out-pointer NULL");
   *out = nullptr;
   if (M < 1 || M > 64) return fail(MDHP_E_ARG, "M = %d outside 1..64", M);
@@ -362,6 +516,10 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
     cudaGetLastError();
     return fail(MDHP_E_NOMEM, "plan allocation failed");
   }
+  if (autotune_cache && autotune_cache[0]) {
+    p->cache = autotune_cache;
+    tune_load(p);
+  }
   *out = p;
   return MDHP_OK;
 }
@@ -413,9 +571,10 @@ mdhp_status mdhp_plan_set_path(mdhp_plan *p, int32_t path) {
 
 mdhp_status mdhp_plan_get_shape(const mdhp_plan *p, int32_t *nt, int32_t *spl, int32_t *cutoff) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
-  if (nt) *nt = p->shape.nt;
+  const bool x = p->use_x && p->xbuf;
+  if (nt) *nt = x ? p->xnt : p->shape.nt;
   if (spl) *spl = p->shape.spl;
-  if (cutoff) *cutoff = p->use_x && p->xbuf ? p->xres : p->shape.cutoff;
+  if (cutoff) *cutoff = x ? p->xres : p->shape.cutoff;
   return MDHP_OK;
 }
 
@@ -603,6 +762,134 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     cudaEventRecord(p->ev_t1, st);
     p->timed = 1;
   }
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit_opts *o,
+                               float *mu, float *alpha, float *beta, double *loglik, int32_t *iters,
+                               int32_t *win_status, int32_t tune_iters, int32_t *chosen,
+                               float *best_ms, void *stream) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  mdhp_status s = check_batch(batch);
+  if (s != MDHP_OK) return s;
+  if (!o) return fail(MDHP_E_ARG, "opts NULL");
+  if (!mu || !alpha || !beta || !loglik || !iters || !win_status)
+    return fail(MDHP_E_ARG, "NULL parameter/output pointer");
+  if (batch->M != p->M || batch->beta_mode != p->beta_mode)
+    return fail(MDHP_E_ARG, "batch does not match plan");
+  const int B = batch->B;
+  if (B == 0) return MDHP_OK;
+  mdhp_fit_opts oo = *o;
+  oo.max_iters = tune_iters > 0 ? tune_iters : 20;
+  oo.tol = 0.0;  // every window runs the same number of iterations
+  const bool learn = oo.fit_beta != 0, adam = oo.optimizer == 1;
+  const int64_t bound = batch->max_events > 0 ? batch->max_events : p->max_events;
+  const int path = (p->use_x && !learn && p->xbuf && bound > 0 && bound <= p->xcap) ? 0 : 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the fit overwrites mu / alpha / beta: keep the caller's values and put
+  // them back before every timed run and at the end
+  const size_t nmu = (size_t)B * p->M, nal = nmu * p->M,
+               nbe = (size_t)B * (p->beta_mode == 0 ? 1 : p->M);
+  float *snap = nullptr;
+  if (cudaMalloc(&snap, (nmu + nal + nbe) * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MDHP_E_NOMEM, "autotune: snapshot allocation failed");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto copy_params = [&](bool save) {
+    float *d[3] = {mu, alpha, beta};
+    const size_t n[3] = {nmu, nal, nbe};
+    size_t off = 0;
+    for (int k = 0; k < 3; ++k) {
+      if (save) cudaMemcpyAsync(snap + off, d[k], n[k] * sizeof(float), cudaMemcpyDeviceToDevice, st);
+      else cudaMemcpyAsync(d[k], snap + off, n[k] * sizeof(float), cudaMemcpyDeviceToDevice, st);
+      off += n[k];
+    }
+  };
+  copy_params(true);
+  struct Cand { int nt, spl, cut; };
+  std::vector<Cand> cands;
+  for (int nt = 64; nt <= 256; nt *= 2) {
+    if (nt < p->Mt) continue;
+    if (path == 0) {
+      const int fit = xres_fit(p, nt, adam);
+      cands.push_back({nt, 0, 0});
+      if (fit >= 128) cands.push_back({nt, 0, fit / 2 / 32 * 32});
+      if (fit >= 64) cands.push_back({nt, 0, fit});
+    } else {
+      for (int spl = 1; spl <= 32; spl *= 2) {
+        if (nt % spl || !get_fit(p->Mt, spl, p->beta_mode, learn, true) ||
+            !get_fit(p->Mt, spl, p->beta_mode, learn, false))
+          continue;
+        const int fit = stage_fit(p, nt, spl, batch->weights != nullptr, learn, adam);
+        const int dflt = default_shape(p->Mt).cutoff;
+        cands.push_back({nt, spl, 0});
+        if (dflt <= fit) cands.push_back({nt, spl, dflt});
+        if (fit >= 64 && fit != dflt) cands.push_back({nt, spl, fit});
+      }
+    }
+  }
+  if (cands.empty()) {
+    cudaFree(snap);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return fail(MDHP_E_UNSUPPORTED, "autotune: no candidate shape for M=%d", p->M);
+  }
+  const Shape shape0 = p->shape;
+  const int xnt0 = p->xnt, xres0 = p->xres, timing0 = p->timing;
+  p->timing = 0;
+  float best = -1.f;
+  Cand win{0, 0, 0};
+  mdhp_status last = MDHP_OK;
+  for (size_t c = 0; c <= cands.size(); ++c) {
+    const Cand cd = cands[c == 0 ? 0 : c - 1];  // run 0 warms the first candidate up
+    const bool okc = path == 0 ? apply_decoupled(p, cd.nt, cd.cut)
+                               : apply_recursion(p, cd.nt, cd.spl, cd.cut);
+    if (!okc) continue;
+    copy_params(false);
+    cudaEventRecord(e0, st);
+    const mdhp_status r = mdhp_fit_batch(p, batch, &oo, mu, alpha, beta, loglik, iters, win_status, stream);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      last = fail(MDHP_E_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    if (r != MDHP_OK) {  // this shape cannot run this batch: skip it
+      last = r;
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (c > 0 && (best < 0.f || ms < best)) {
+      best = ms;
+      win = cd;
+    }
+  }
+  p->timing = timing0;
+  p->shape = shape0;
+  p->xnt = xnt0;
+  p->xres = xres0;
+  copy_params(false);
+  cudaStreamSynchronize(st);
+  cudaFree(snap);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0.f)
+    return last != MDHP_OK ? last : fail(MDHP_E_UNSUPPORTED, "autotune: no candidate shape ran");
+  if (path == 0) apply_decoupled(p, win.nt, win.cut);
+  else apply_recursion(p, win.nt, win.spl, win.cut);
+  if (chosen) {
+    chosen[0] = path;
+    chosen[1] = win.nt;
+    chosen[2] = win.spl;
+    chosen[3] = win.cut;
+  }
+  if (best_ms) *best_ms = best;
+  if (!tune_store(p, path, win.nt, win.spl, win.cut, best))
+    return fail(MDHP_E_ARG, "autotune: cannot write the cache file %s", p->cache.c_str());
   return MDHP_OK;
 }
 
