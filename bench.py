@@ -230,7 +230,7 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    from paper_2411_10258_gb300 import DeviceBatch, FitOptions, Plan
+    from paper_2411_10258_gb300 import DeviceBatch, FitOptions, Plan, shard
     from paper_2411_10258_gb300 import build as libbuild
 
     if not os.path.exists(os.path.join(ROOT, "paper_2411_10258_gb300", "_build", "libmdhp.so")):
@@ -281,10 +281,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = float(np.sum(step_ms))
     kern_avg = float(np.mean(kern_ms))
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = shard.max_over_ranks(tot_ms, device=dev)  # whole-job time: the slowest rank
     value = world * B * args.steps / (tot_ms / 1000.0)
     events_iters = float(bt.n_events) * args.iters
     llg_events_per_s = events_iters / (kern_avg / 1000.0)
