@@ -50,7 +50,7 @@ typedef enum {
   MDHP_E_TIME_RANGE = 4,   /* a timestamp outside [0, T_span], or T_span < 0 / not finite */
   MDHP_E_NONFINITE = 5,    /* NaN/Inf in inputs, or lnL / gradient not finite */
   MDHP_E_MAXITER = 6,      /* fit: tolerance requested but not met within max_iters */
-  MDHP_E_TIMEOUT = 7,      /* reserved: a bounded device-side wait gave up */
+  MDHP_E_TIMEOUT = 7,      /* a bounded device-side wait gave up (window results invalid) */
   MDHP_E_CUDA = 8,         /* a CUDA call failed */
   MDHP_E_NOMEM = 9,        /* plan allocation failed */
   MDHP_E_UNSUPPORTED = 10, /* valid request this build does not implement */
@@ -207,14 +207,16 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
  * with `opts` for each candidate launch shape and keeps the fastest in the
  * plan.  Candidates: 64, 128 and 256 threads per window; for the decoupled
  * fixed-beta kernels the shared-memory class (none, half, the largest that
- * fits); for the event recursion every built threads-per-chunk split and the
+ * fits) and the feature ring (none; 1x4, 2x3, 2x4, 4x3 steps x stages); for
+ * the event recursion every built threads-per-chunk split and the
  * staging cutoff (none, the default, the largest that fits).  Each candidate
  * runs tune_iters iterations (<= 0: 20) with tol = 0 after one warm-up run.
  *   mu, alpha, beta  device, as for mdhp_fit_batch; used as the starting point
  *                    when opts->init == 0 and restored on return
  *   loglik, iters, win_status  device scratch, overwritten
- *   chosen   int32[4] host or NULL: path (0 decoupled, 1 recursion), threads
- *            per window, threads per chunk (0 for decoupled), cutoff
+ *   chosen   int32[6] host or NULL: path (0 decoupled, 1 recursion), threads
+ *            per window, threads per chunk (0 for decoupled), cutoff, and the
+ *            feature ring's steps per stage and stages (mdhp_plan_set_pipeline)
  *   best_ms  float host or NULL: device time of the chosen shape
  * When the plan was created with an autotune_cache path, the choice is
  * written there under a key of the device name and compute capability, M,
@@ -305,6 +307,21 @@ mdhp_status mdhp_plan_set_init_model(mdhp_plan *plan, mdhp_init_model *model);
 #define MDHP_PATH_AUTO 0
 #define MDHP_PATH_RECURSION 1
 mdhp_status mdhp_plan_set_path(mdhp_plan *plan, int32_t path);
+
+/* Streaming of the decoupled kernels' features (fixed beta, windows longer
+ * than the shared-memory class): the features of each window are re-read
+ * every iteration from the plan's device scratch.  With stages > 0 they pass
+ * through a ring of `stages` shared-memory buffers of `steps_per_stage` steps
+ * each (a step is one feature row per thread), filled by bulk asynchronous
+ * copies that run up to `stages` buffers ahead, across iterations; stages = 0
+ * reads them through L1 with a one-step register prefetch.  stages 0..8,
+ * steps_per_stage 1..16.  Default 0 stages (register prefetch measured
+ * faster on the 4,096-window M=16 and M=32 workloads); a ring that does not
+ * fit the block's shared memory falls back to stages = 0 for that launch.
+ * Results do not depend on the choice. */
+mdhp_status mdhp_plan_set_pipeline(mdhp_plan *plan, int32_t steps_per_stage, int32_t stages);
+mdhp_status mdhp_plan_get_pipeline(const mdhp_plan *plan, int32_t *steps_per_stage,
+                                   int32_t *stages);
 
 /*
  * Batched fit without a plan and without allocating device memory.  (An

@@ -211,7 +211,7 @@ class Plan:
         scratch = dict(loglik=torch.empty(B, dtype=torch.float64, device=dev),
                        iters=torch.empty(B, dtype=torch.int32, device=dev),
                        status=torch.empty(B, dtype=torch.int32, device=dev))
-        chosen = (ctypes.c_int32 * 4)()
+        chosen = (ctypes.c_int32 * 6)()
         best = ctypes.c_float(-1.0)
         st = db.c_struct()
         o = opts.c_struct()
@@ -221,7 +221,19 @@ class Plan:
                                          int(tune_iters), chosen, ctypes.byref(best), _stream(stream))
         _lib.check(rc, "mdhp_plan_autotune")
         return dict(path=("decoupled", "recursion")[chosen[0]], threads_per_window=chosen[1],
-                    threads_per_chunk=chosen[2], cutoff=chosen[3], ms=best.value)
+                    threads_per_chunk=chosen[2], cutoff=chosen[3], pipe_steps=chosen[4],
+                    pipe_stages=chosen[5], ms=best.value)
+
+    def set_pipeline(self, steps_per_stage: int, stages: int):
+        """Feature ring of the decoupled kernels (mdhp_plan_set_pipeline); stages=0: none."""
+        _lib.check(self.lib.mdhp_plan_set_pipeline(self.h, steps_per_stage, stages),
+                   "mdhp_plan_set_pipeline")
+
+    def pipeline(self):
+        v = [ctypes.c_int32() for _ in range(2)]
+        _lib.check(self.lib.mdhp_plan_get_pipeline(self.h, *[ctypes.byref(x) for x in v]),
+                   "mdhp_plan_get_pipeline")
+        return tuple(x.value for x in v)
 
     def fit(self, db: DeviceBatch, opts: FitOptions, mu: torch.Tensor, alpha: torch.Tensor,
             beta: torch.Tensor, out: dict | None = None, stream=None) -> dict:

@@ -17,9 +17,17 @@ FitFn get_fit_m32(int SPL, int BM, bool learn, bool stage) {
 
 WgFn get_wg_m32(int BM) { return BM == 0 ? k_weight_grad<32, 0> : k_weight_grad<32, 1>; }
 
-FitFn get_fitx_m32(int BM, bool xs) {
-  if (BM == 0) return xs ? k_fit_x<32, 0, true> : k_fit_x<32, 0, false>;
-  return xs ? k_fit_x<32, 1, true> : k_fit_x<32, 1, false>;
+FitFn get_fitx_m32(int BM, int xm, int nt) {
+  if (BM != 0 && BM != 1) return nullptr;
+  if (xm == XM_SHARED) return BM == 0 ? k_fit_x<32, 0, XM_SHARED, 0> : k_fit_x<32, 1, XM_SHARED, 0>;
+  if (xm == XM_RING) return BM == 0 ? k_fit_x<32, 0, XM_RING, 0> : k_fit_x<32, 1, XM_RING, 0>;
+  if (xm != XM_GLOBAL) return nullptr;
+  switch (nt) {  // block size compiled in: constant-offset feature loads
+    case 64: return BM == 0 ? k_fit_x<32, 0, XM_GLOBAL, 64> : k_fit_x<32, 1, XM_GLOBAL, 64>;
+    case 128: return BM == 0 ? k_fit_x<32, 0, XM_GLOBAL, 128> : k_fit_x<32, 1, XM_GLOBAL, 128>;
+    case 256: return BM == 0 ? k_fit_x<32, 0, XM_GLOBAL, 256> : k_fit_x<32, 1, XM_GLOBAL, 256>;
+  }
+  return nullptr;
 }
 
 }  // namespace mdhp

@@ -17,6 +17,6 @@ FitFn get_fit_m64(int SPL, int BM, bool learn, bool stage) {
 
 WgFn get_wg_m64(int BM) { return BM == 0 ? k_weight_grad<64, 0> : k_weight_grad<64, 1>; }
 
-FitFn get_fitx_m64(int, bool) { return nullptr; }
+FitFn get_fitx_m64(int, int, int) { return nullptr; }
 
 }  // namespace mdhp

@@ -66,13 +66,13 @@ FitFn get_fit(int M, int SPL, int BM, bool learn, bool stage) {
   }
   return nullptr;
 }
-FitFn get_fitx(int M, int BM, bool xs) {
+FitFn get_fitx(int M, int BM, int xm, int nt) {
   switch (M) {
-    case 4: return get_fitx_m4(BM, xs);
-    case 8: return get_fitx_m8(BM, xs);
-    case 16: return get_fitx_m16(BM, xs);
-    case 32: return get_fitx_m32(BM, xs);
-    case 64: return get_fitx_m64(BM, xs);
+    case 4: return get_fitx_m4(BM, xm, nt);
+    case 8: return get_fitx_m8(BM, xm, nt);
+    case 16: return get_fitx_m16(BM, xm, nt);
+    case 32: return get_fitx_m32(BM, xm, nt);
+    case 64: return get_fitx_m64(BM, xm, nt);
   }
   return nullptr;
 }
@@ -170,6 +170,9 @@ struct mdhp_plan {
   int xres = 0, xrgrid = 0;  // windows of <= xres events keep their features in shared memory
   int xres_max = 0;          // largest shared-memory class the device allows
   int use_x = 1;  // 0 forces the recursion kernels (for tests and comparisons)
+  // streamed features of the decoupled kernels: ring of pipe_stages shared-memory
+  // buffers of pipe_steps steps filled by bulk copies (0 stages: register prefetch)
+  int pipe_steps = 0, pipe_stages = 0;  // measured: register prefetch is faster on the bench workloads
   mdhp_init_model *model = nullptr;  // learned initializer (not owned)
   std::string cache;                 // autotune cache file ("" = none)
 };
@@ -179,7 +182,8 @@ struct mdhp_plan {
 // The cache is a small JSON file, one entry per line:
 //   {"format": "mdhp-autotune-1", "entries": [
 //   {"key": "<device>|sm<cc>|M<M>|mode<m>|W<max_windows>|E<max_events>|<path>",
-//    "threads_per_window": 64, "threads_per_chunk": 0, "smem_cutoff_events": 0, "ms": 14.8},
+//    "threads_per_window": 64, "threads_per_chunk": 0, "smem_cutoff_events": 0,
+//    "pipe_steps": 2, "pipe_stages": 3, "ms": 14.8},
 //   ...]}
 // keyed by the device and the plan's creation arguments; <path> is "decoupled"
 // (fixed-beta features kernels: threads per window and the shared-memory
@@ -286,14 +290,22 @@ void tune_load(mdhp_plan *p) {
       const int nt = field_int(e.second, "threads_per_window", 0);
       const int spl = field_int(e.second, "threads_per_chunk", 0);
       const int cut = field_int(e.second, "smem_cutoff_events", -1);
-      if (path == 0 && p->xbuf) apply_decoupled(p, nt, cut);
+      if (path == 0 && p->xbuf && apply_decoupled(p, nt, cut)) {
+        const int pd = field_int(e.second, "pipe_stages", p->pipe_stages);
+        const int ps = field_int(e.second, "pipe_steps", p->pipe_steps);
+        if (pd == 0 || (pd > 0 && pd <= 8 && ps >= 1 && ps <= 16)) {
+          p->pipe_stages = pd;
+          p->pipe_steps = pd > 0 ? ps : 0;
+        }
+      }
       if (path == 1) apply_recursion(p, nt, spl, cut);
     }
   }
   cudaGetLastError();
 }
 
-bool tune_store(const mdhp_plan *p, int path, int nt, int spl, int cutoff, float ms) {
+bool tune_store(const mdhp_plan *p, int path, int nt, int spl, int cutoff, int ps, int pd,
+                float ms) {
   if (p->cache.empty()) return true;
   std::string text;
   read_text(p->cache, text);
@@ -302,8 +314,8 @@ bool tune_store(const mdhp_plan *p, int path, int nt, int spl, int cutoff, float
   char line[768];
   snprintf(line, sizeof(line),
            "{\"key\": \"%s\", \"threads_per_window\": %d, \"threads_per_chunk\": %d, "
-           "\"smem_cutoff_events\": %d, \"ms\": %.4f}",
-           key.c_str(), nt, spl, cutoff, ms);
+           "\"smem_cutoff_events\": %d, \"pipe_steps\": %d, \"pipe_stages\": %d, \"ms\": %.4f}",
+           key.c_str(), nt, spl, cutoff, ps, pd, ms);
   bool found = false;
   for (auto &e : v)
     if (e.first == key) {
@@ -459,10 +471,10 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
     ok &= cudaMalloc(&p->sort_tmp, p->sort_tmp_bytes > 0 ? p->sort_tmp_bytes : 16) == cudaSuccess;
   }
   if (ok && p->Mt <= 32 && max_events_per_window > 0 && max_events_per_window < (1 << 26)) {
-    FitFn fx = get_fitx(p->Mt, beta_mode, false);
     // scratch slots for the largest resident grid over the supported block sizes
     int slots = 0;
     for (int nt = 64; nt <= 256; nt *= 2) {
+      FitFn fx = get_fitx(p->Mt, beta_mode, XM_GLOBAL, nt);
       const Carve cx = make_carve_x(p->Mt, nt, 0, true);
       int occ = 0;
       if (fx && prepare_kernel((const void *)fx, cx.total) == MDHP_OK &&
@@ -484,7 +496,7 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
       }
     }
     // shared-memory class: two CTAs per SM for M <= 16, one for M = 32
-    FitFn fr = get_fitx(p->Mt, beta_mode, true);
+    FitFn fr = get_fitx(p->Mt, beta_mode, XM_SHARED, p->xnt);
     const int fixed = make_carve_x(p->Mt, p->xnt, 0, true).total;
     const int target = (p->Mt <= 16 ? max_dyn_smem() / 2 : max_dyn_smem()) - 1024;
     int cap = (target - fixed) / (p->Mt * 4);
@@ -566,6 +578,23 @@ mdhp_status mdhp_plan_set_path(mdhp_plan *p, int32_t path) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
   if (path != MDHP_PATH_AUTO && path != MDHP_PATH_RECURSION) return fail(MDHP_E_ARG, "path %d", path);
   p->use_x = path == MDHP_PATH_AUTO ? 1 : 0;
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_plan_set_pipeline(mdhp_plan *p, int32_t steps_per_stage, int32_t stages) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  if (stages < 0 || stages > 8) return fail(MDHP_E_ARG, "stages %d (0..8)", stages);
+  if (stages > 0 && (steps_per_stage < 1 || steps_per_stage > 16))
+    return fail(MDHP_E_ARG, "steps per stage %d (1..16)", steps_per_stage);
+  p->pipe_stages = stages;
+  p->pipe_steps = stages > 0 ? steps_per_stage : 0;
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_plan_get_pipeline(const mdhp_plan *p, int32_t *steps_per_stage, int32_t *stages) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  if (steps_per_stage) *steps_per_stage = p->pipe_steps;
+  if (stages) *stages = p->pipe_stages;
   return MDHP_OK;
 }
 
@@ -679,12 +708,18 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     const bool any_long = !(xres > 0 && bound <= xres);
     if (p->timing && !t0_done) cudaEventRecord(p->ev_t0, st);
     if (any_long) {
-      FitFn fx = get_fitx(p->Mt, p->beta_mode, false);
       FitArgs al = ax;
       al.queue = p->ctl + 0;
       al.range = p->ctl + 2;
       al.ev_cap = p->xcap;
-      al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1);
+      al.pipe_steps = p->pipe_steps;
+      al.pipe_stages = p->pipe_stages;
+      al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1, p->pipe_steps, p->pipe_stages);
+      if (al.pipe_stages > 0 && al.carve.total > max_dyn_smem()) {  // ring too large for this block
+        al.pipe_stages = 0;
+        al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1);
+      }
+      FitFn fx = get_fitx(p->Mt, p->beta_mode, al.pipe_stages > 0 ? XM_RING : XM_GLOBAL, p->xnt);
       if ((s = prepare_kernel((const void *)fx, al.carve.total)) != MDHP_OK) return s;
       cudaStream_t ls = st;
       if (xres > 0) {
@@ -701,7 +736,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
       if (xres > 0) cudaEventRecord(p->ev_join, p->side);
     }
     if (xres > 0) {
-      FitFn fr = get_fitx(p->Mt, p->beta_mode, true);
+      FitFn fr = get_fitx(p->Mt, p->beta_mode, XM_SHARED, p->xnt);
       FitArgs ar = ax;
       ar.queue = p->ctl + 1;
       ar.range = p->ctl + 4;
@@ -809,15 +844,19 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
     }
   };
   copy_params(true);
-  struct Cand { int nt, spl, cut; };
+  struct Cand { int nt, spl, cut, ps, pd; };
   std::vector<Cand> cands;
+  static const int kPipes[][2] = {{0, 0}, {1, 4}, {2, 3}, {2, 4}, {4, 3}};
   for (int nt = 64; nt <= 256; nt *= 2) {
     if (nt < p->Mt) continue;
     if (path == 0) {
       const int fit = xres_fit(p, nt, adam);
-      cands.push_back({nt, 0, 0});
-      if (fit >= 128) cands.push_back({nt, 0, fit / 2 / 32 * 32});
-      if (fit >= 64) cands.push_back({nt, 0, fit});
+      for (const auto &pd : kPipes) {
+        if (pd[1] > 0 && make_carve_x(p->Mt, nt, 0, adam, pd[0], pd[1]).total > max_dyn_smem()) continue;
+        cands.push_back({nt, 0, 0, pd[0], pd[1]});
+        if (fit >= 64) cands.push_back({nt, 0, fit, pd[0], pd[1]});
+      }
+      if (fit >= 128) cands.push_back({nt, 0, fit / 2 / 32 * 32, p->pipe_steps, p->pipe_stages});
     } else {
       for (int spl = 1; spl <= 32; spl *= 2) {
         if (nt % spl || !get_fit(p->Mt, spl, p->beta_mode, learn, true) ||
@@ -825,9 +864,9 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
           continue;
         const int fit = stage_fit(p, nt, spl, batch->weights != nullptr, learn, adam);
         const int dflt = default_shape(p->Mt).cutoff;
-        cands.push_back({nt, spl, 0});
-        if (dflt <= fit) cands.push_back({nt, spl, dflt});
-        if (fit >= 64 && fit != dflt) cands.push_back({nt, spl, fit});
+        cands.push_back({nt, spl, 0, p->pipe_steps, p->pipe_stages});
+        if (dflt <= fit) cands.push_back({nt, spl, dflt, p->pipe_steps, p->pipe_stages});
+        if (fit >= 64 && fit != dflt) cands.push_back({nt, spl, fit, p->pipe_steps, p->pipe_stages});
       }
     }
   }
@@ -839,15 +878,18 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
   }
   const Shape shape0 = p->shape;
   const int xnt0 = p->xnt, xres0 = p->xres, timing0 = p->timing;
+  const int ps0 = p->pipe_steps, pd0 = p->pipe_stages;
   p->timing = 0;
   float best = -1.f;
-  Cand win{0, 0, 0};
+  Cand win{0, 0, 0, 0, 0};
   mdhp_status last = MDHP_OK;
   for (size_t c = 0; c <= cands.size(); ++c) {
     const Cand cd = cands[c == 0 ? 0 : c - 1];  // run 0 warms the first candidate up
     const bool okc = path == 0 ? apply_decoupled(p, cd.nt, cd.cut)
                                : apply_recursion(p, cd.nt, cd.spl, cd.cut);
     if (!okc) continue;
+    p->pipe_steps = cd.ps;
+    p->pipe_stages = cd.pd;
     copy_params(false);
     cudaEventRecord(e0, st);
     const mdhp_status r = mdhp_fit_batch(p, batch, &oo, mu, alpha, beta, loglik, iters, win_status, stream);
@@ -872,6 +914,8 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
   p->shape = shape0;
   p->xnt = xnt0;
   p->xres = xres0;
+  p->pipe_steps = ps0;
+  p->pipe_stages = pd0;
   copy_params(false);
   cudaStreamSynchronize(st);
   cudaFree(snap);
@@ -879,16 +923,23 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
   cudaEventDestroy(e1);
   if (best < 0.f)
     return last != MDHP_OK ? last : fail(MDHP_E_UNSUPPORTED, "autotune: no candidate shape ran");
-  if (path == 0) apply_decoupled(p, win.nt, win.cut);
-  else apply_recursion(p, win.nt, win.spl, win.cut);
+  if (path == 0) {
+    apply_decoupled(p, win.nt, win.cut);
+    p->pipe_steps = win.ps;
+    p->pipe_stages = win.pd;
+  } else {
+    apply_recursion(p, win.nt, win.spl, win.cut);
+  }
   if (chosen) {
     chosen[0] = path;
     chosen[1] = win.nt;
     chosen[2] = win.spl;
     chosen[3] = win.cut;
+    chosen[4] = path == 0 ? win.ps : 0;
+    chosen[5] = path == 0 ? win.pd : 0;
   }
   if (best_ms) *best_ms = best;
-  if (!tune_store(p, path, win.nt, win.spl, win.cut, best))
+  if (!tune_store(p, path, win.nt, win.spl, win.cut, win.ps, win.pd, best))
     return fail(MDHP_E_ARG, "autotune: cannot write the cache file %s", p->cache.c_str());
   return MDHP_OK;
 }

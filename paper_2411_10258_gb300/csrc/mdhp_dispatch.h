@@ -16,14 +16,17 @@ using WgFn = void (*)(WgArgs);
 LlgFn get_llg(int M, int SPL, int BM, bool learn, bool stage);
 FitFn get_fit(int M, int SPL, int BM, bool learn, bool stage);
 WgFn get_wg(int M, int BM);
-FitFn get_fitx(int M, int BM, bool xs);
+// decoupled fit: xm = XM_GLOBAL (features streamed, register prefetch; built
+// for block sizes nt = 64, 128, 256), XM_SHARED (features in shared memory)
+// or XM_RING (streamed through a bulk-copy ring); nt is ignored for the last two
+FitFn get_fitx(int M, int BM, int xm, int nt);
 void record_error(const char *msg);
 
 #define MDHP_DECLARE_M(MV)                                                   \
   LlgFn get_llg_m##MV(int SPL, int BM, bool learn, bool stage);              \
   FitFn get_fit_m##MV(int SPL, int BM, bool learn, bool stage);              \
   WgFn get_wg_m##MV(int BM);                                                 \
-  FitFn get_fitx_m##MV(int BM, bool xs);
+  FitFn get_fitx_m##MV(int BM, int xm, int nt);
 MDHP_DECLARE_M(4)
 MDHP_DECLARE_M(8)
 MDHP_DECLARE_M(16)

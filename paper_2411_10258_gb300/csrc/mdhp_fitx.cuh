@@ -19,6 +19,7 @@
 // Part2 + Part3 use the compensator constants of the state at T_span.
 #pragma once
 
+#include "mdhp_async.cuh"
 #include "mdhp_solver.cuh"
 
 namespace mdhp {
@@ -98,45 +99,43 @@ __device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, in
   __syncthreads();
 }
 
-// One evaluation over the sorted features: this thread's range [p0, p1),
-// starting in type i0.  Segment sums go to P[(tid + i) * (M + 4) + 0..M].
-template <int M, bool XS, typename XP>
-__device__ __forceinline__ void xpass(int p0, int p1, int i0, XP X, int xcap, XMap m,
-                                      const Sm<M> &sm, float &Ls, float &Lc) {
-  constexpr int NQ = M / 4;
-  constexpr int AP = M + 4;
-  constexpr int PP = M + 4;
-  if (p0 >= p1) return;
-  const int tid = threadIdx.x;
-  int i = i0;
-  int te = sm.tstart[i + 1];
-  float4 ar[NQ];
-  float mu = sm.mu[i];
+// Per-thread state of one evaluation over the sorted features: the current
+// type i (its row alpha_i and mu_i in registers), the running sums of its
+// gradient, and the segment flush when the thread's range crosses into the
+// next type.  Segment sums go to P[(tid + i) * (M + 4) + 0..M].
+template <int M>
+struct XAcc {
+  static constexpr int NQ = M / 4;
+  static constexpr int AP = M + 4;
+  static constexpr int PP = M + 4;
+  int i, te;
+  float mu, gm;
+  float4 ar[NQ], g[NQ];
+
+  __device__ __forceinline__ void begin(int i0, const Sm<M> &sm) {
+    i = i0;
+    te = sm.tstart[i + 1];
+    mu = sm.mu[i];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) ar[q] = reinterpret_cast<const float4 *>(sm.alpha + i * AP)[q];
-  float4 g[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) g[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  float gm = 0.f;
-  float4 xn[NQ];  // next position's features, loaded one step ahead
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) xn[q] = X[xidx<XS>(q, p0, xcap, NQ, m)];
-  for (int p = p0; p < p1; ++p) {
-    float4 x[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) x[q] = xn[q];
-    if (p + 1 < p1) {
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) xn[q] = X[xidx<XS>(q, p + 1, xcap, NQ, m)];
+    for (int q = 0; q < NQ; ++q) {
+      ar[q] = reinterpret_cast<const float4 *>(sm.alpha + i * AP)[q];
+      g[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    while (p >= te) {  // leave type i (types with no events are passed over)
-      float4 *slot = reinterpret_cast<float4 *>(sm.P + (tid + i) * PP);
+    gm = 0.f;
+  }
+  __device__ __forceinline__ void flush(const Sm<M> &sm) {
+    float4 *slot = reinterpret_cast<float4 *>(sm.P + (threadIdx.x + i) * PP);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        slot[q] = g[q];
-        g[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      sm.P[(tid + i) * PP + M] = gm;
+    for (int q = 0; q < NQ; ++q) slot[q] = g[q];
+    sm.P[(threadIdx.x + i) * PP + M] = gm;
+  }
+  // the event at sorted position p with features x
+  __device__ __forceinline__ void event(int p, const float4 (&x)[NQ], const Sm<M> &sm, float &Ls,
+                                        float &Lc) {
+    while (p >= te) {  // leave type i (types with no events are passed over)
+      flush(sm);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) g[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       gm = 0.f;
       ++i;
       te = sm.tstart[i + 1];
@@ -164,10 +163,124 @@ __device__ __forceinline__ void xpass(int p0, int p1, int i0, XP X, int xcap, XM
       g[q].w = fmaf(r, x[q].w, g[q].w);
     }
   }
-  float4 *slot = reinterpret_cast<float4 *>(sm.P + (tid + i) * PP);
+};
+
+// One evaluation over the sorted features: this thread's range [p0, p1),
+// starting in type i0, features read directly (shared memory, or global
+// memory one step ahead in registers).  Two events per trip with two
+// register buffers (no copies between them); with the block size a
+// compile-time constant (NTC > 0) every global load is base + constant.
+template <int M, bool XS, int NTC, typename XP>
+__device__ __forceinline__ void xpass(int p0, int p1, int i0, XP X, int xcap, XMap m,
+                                      const Sm<M> &sm, float &Ls, float &Lc) {
+  constexpr int NQ = M / 4;
+  if (p0 >= p1) return;
+  XAcc<M> acc;
+  acc.begin(i0, sm);
+  // slice q of position p: shared X[q * xcap + p]; global (step-major, this
+  // thread's column) X[((p - p0) * NQ + q) * NT + tid]
+  const int NT = NTC > 0 ? NTC : m.NT;
+  const int qs = XS ? xcap : NT;
+  const int ps = XS ? 1 : NQ * NT;
+  const float4 *px = XS ? X + p0 : X + threadIdx.x;
+  float4 xa[NQ], xb[NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) slot[q] = g[q];
-  sm.P[(tid + i) * PP + M] = gm;
+  for (int q = 0; q < NQ; ++q) xa[q] = px[q * qs];
+  int p = p0;
+  for (;;) {
+    const bool hb = p + 1 < p1;
+    if (hb) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) xb[q] = px[ps + q * qs];
+    }
+    acc.event(p, xa, sm, Ls, Lc);
+    if (!hb) break;
+    const bool ha = p + 2 < p1;
+    if (ha) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) xa[q] = px[2 * ps + q * qs];
+    }
+    acc.event(p + 1, xb, sm, Ls, Lc);
+    if (!ha) break;
+    p += 2;
+    px += 2 * ps;
+  }
+  acc.flush(sm);
+}
+
+// Streamed features through a ring of shared-memory buffers filled by bulk
+// copies.  In the step-major global layout, step k of every thread is one
+// contiguous block of NQ * NT float4, so S consecutive steps are one copy.
+// The copies form an endless cyclic sequence over the window's stages (the
+// features do not change between iterations), so the ring runs ahead across
+// iteration boundaries; fill g holds stage (g - base) mod nst and lands in
+// buffer g mod D, whose mbarrier completes for the (g / D)-th time.
+struct XPipe {
+  const float4 *src;  // the CTA's global feature slot
+  int step_f4;        // float4 per step (NQ * NT)
+  int L, S, D, nst;   // steps per pass, steps per stage, buffers, stages per pass
+  uint32_t used, issued, base;  // fills consumed (all threads) / issued (thread 0)
+};
+
+template <int M>
+__device__ __forceinline__ void xpipe_issue(XPipe &pp, const Sm<M> &sm) {
+  const uint32_t g = pp.issued++;
+  const int c = (int)((g - pp.base) % (uint32_t)pp.nst);
+  const int slot = (int)(g % (uint32_t)pp.D);
+  const int k0 = c * pp.S;
+  const int ns = min(pp.S, pp.L - k0);
+  const uint32_t bytes = (uint32_t)ns * (uint32_t)pp.step_f4 * 16u;
+  uint64_t *bar = sm.mbar + slot;
+  mbar_expect_tx(bar, bytes);
+  bulk_copy_g2s(sm.ring + (size_t)slot * pp.S * pp.step_f4, pp.src + (size_t)k0 * pp.step_f4,
+                bytes, bar);
+}
+
+// One evaluation through the ring.  Every thread walks all stages (threads
+// without positions only keep step); a barrier closes each stage, after which
+// thread 0 refills its buffer D fills ahead.  Returns false (uniformly) if a
+// fill did not arrive within the wait bound.
+template <int M>
+__device__ __forceinline__ bool xpass_pipe(int p0, int p1, int i0, XPipe &pp, const Sm<M> &sm,
+                                           float &Ls, float &Lc) {
+  constexpr int NQ = M / 4;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const bool active = p0 < p1;
+  XAcc<M> acc;
+  if (active) acc.begin(i0, sm);
+  for (int s = 0; s < pp.nst; ++s) {
+    const uint32_t g = pp.used;
+    const int slot = (int)(g % (uint32_t)pp.D);
+    if (!mbar_wait(sm.mbar + slot, (g / (uint32_t)pp.D) & 1u)) sm.ctl[3] = 1;
+    const float4 *buf = sm.ring + (size_t)slot * pp.S * pp.step_f4 + tid;
+    const int k0 = s * pp.S, k1 = min(k0 + pp.S, pp.L);
+    if (active) {
+      for (int k = k0; k < k1; ++k) {
+        const int p = p0 + k;
+        if (p >= p1) break;
+        float4 x[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) x[q] = buf[(k - k0) * pp.step_f4 + q * NT];
+        acc.event(p, x, sm, Ls, Lc);
+      }
+    }
+    __syncthreads();
+    ++pp.used;
+    if (sm.ctl[3]) return false;
+    if (tid == 0) xpipe_issue<M>(pp, sm);
+  }
+  if (active) acc.flush(sm);
+  return true;
+}
+
+// Waits out the D fills still in flight when a window is done (bounded).
+template <int M>
+__device__ __forceinline__ void xpipe_drain(XPipe &pp, const Sm<M> &sm) {
+  for (int d = 0; d < pp.D; ++d) {
+    const uint32_t g = pp.used++;
+    mbar_wait(sm.mbar + (g % (uint32_t)pp.D), (g / (uint32_t)pp.D) & 1u);
+  }
+  __syncthreads();
 }
 
 // Event part of the gradient of parameter p (mu_i or alpha_ij): the sum of
@@ -181,8 +294,11 @@ __device__ __forceinline__ float xseg_sum(int i, int j, const Sm<M> &sm) {
   return acc;
 }
 
-template <int M, int BM, bool XS>
+enum : int { XM_GLOBAL = 0, XM_SHARED = 1, XM_RING = 2 };
+
+template <int M, int BM, int XM, int NTC>
 __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
+  constexpr bool XS = XM == XM_SHARED;
   extern __shared__ __align__(16) unsigned char smem[];
   Sm<M> sm;
   sm.bind(smem, a.carve);
@@ -191,10 +307,19 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
   const int nb = BM == 0 ? 1 : Mrt;
   const int np = Mrt + Mrt * Mrt + nb;
   const int nupd = Mrt + Mrt * Mrt;
-  const int tid = threadIdx.x, NT = blockDim.x;
+  const int tid = threadIdx.x, NT = NTC > 0 ? NTC : (int)blockDim.x;
   const int xcap = a.ev_cap;
   // global slot: (xcap + 2 NT) rows, enough for L * NT with the odd rounding of L
   float4 *Xg = XS ? nullptr : a.xbuf + (size_t)blockIdx.x * (M / 4) * (size_t)(xcap + 2 * NT);
+  constexpr bool pipe = XM == XM_RING;
+  XPipe pp{Xg, (M / 4) * NT, 1, a.pipe_steps, a.pipe_stages, 1, 0u, 0u, 0u};
+  if (pipe) {
+    if (tid == 0) {
+      for (int d = 0; d < pp.D; ++d) mbar_init(sm.mbar + d, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+  }
   for (;;) {
     if (tid == 0) sm.ctl[1] = atomicAdd(a.queue, 1);
     __syncthreads();
@@ -245,6 +370,7 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     const XMap xm{L, NT};
     if (XS) build_features<M, BM, true>(N, ev, Mrt, sm, sm.xs, xcap, xm);
     else build_features<M, BM, false>(N, ev, Mrt, sm, Xg, xcap, xm);
+    if (pipe) fence_proxy_async_global();  // this thread's feature stores -> the copy engine
     const int p0 = min(tid * L, N), p1 = min(p0 + L, N);
     int i0 = 0;
     while (i0 < M - 1 && sm.tstart[i0 + 1] <= p0) ++i0;
@@ -252,7 +378,17 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
       sm.tf[i] = sm.tstart[i] / L;
       sm.tl[i] = sm.tstart[i + 1] > sm.tstart[i] ? (sm.tstart[i + 1] - 1) / L : -1;
     }
+    if (tid == 0) sm.ctl[3] = 0;
     __syncthreads();
+    if (pipe) {  // start the ring: the first D fills of this window's cyclic stage sequence
+      pp.L = L;
+      pp.nst = (L + pp.S - 1) / pp.S;
+      pp.base = pp.used;
+      if (tid == 0) {
+        pp.issued = pp.used;
+        for (int d = 0; d < pp.D; ++d) xpipe_issue<M>(pp, sm);
+      }
+    }
     const float invN = 1.f / (float)max(N, 1);
     double lnl_prev = 0.0, lnl_out = 0.0;
     int streak = 0, k = 0;
@@ -260,8 +396,21 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     float b1t = 1.f, b2t = 1.f;
     for (k = 0; k < a.max_iters; ++k) {
       float Ls = 0.f, Lc = 0.f;
-      if (XS) xpass<M, true>(p0, p1, i0, (const float4 *)sm.xs, xcap, xm, sm, Ls, Lc);
-      else xpass<M, false>(p0, p1, i0, (const float4 *)Xg, xcap, xm, sm, Ls, Lc);
+      if (XS) {
+        xpass<M, true, 0>(p0, p1, i0, (const float4 *)sm.xs, xcap, xm, sm, Ls, Lc);
+      } else if constexpr (pipe) {
+        if (!xpass_pipe<M>(p0, p1, i0, pp, sm, Ls, Lc)) {  // a fill never arrived
+          if (tid == 0) {
+            a.status[b] = kE_TIMEOUT;
+            a.loglik[b] = __longlong_as_double(0x7ff8000000000000LL);
+            a.iters[b] = k;
+          }
+          xpipe_drain<M>(pp, sm);
+          return;
+        }
+      } else {
+        xpass<M, false, NTC>(p0, p1, i0, (const float4 *)Xg, xcap, xm, sm, Ls, Lc);
+      }
       // Part2 + Part3 and the block sums (ends with a barrier)
       float Ps = 0.f, Pc = 0.f;
       for (int p = tid; p < M + M * M; p += NT) {  // padded entries hold zeros
@@ -346,6 +495,7 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
         break;
       }
     }
+    if (pipe) xpipe_drain<M>(pp, sm);  // the fills issued ahead for an iteration that never ran
     for (int p = tid; p < Mrt * Mrt; p += NT)
       a.alpha[(int64_t)b * Mrt * Mrt + p] = sm.alpha[(p / Mrt) * AP + (p % Mrt)];
     for (int i = tid; i < Mrt; i += NT) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];

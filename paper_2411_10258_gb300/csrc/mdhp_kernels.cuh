@@ -40,6 +40,7 @@ struct FitArgs {
   float lr, mu_floor, alpha_floor, beta_floor, b1, b2, eps;
   double tol;
   float4 *xbuf;  // decoupled fit: per-CTA feature scratch (global), or nullptr
+  int pipe_steps, pipe_stages;  // streamed features: bulk-copy ring (0 stages: register prefetch)
   Carve carve;
 };
 

@@ -45,7 +45,7 @@ constexpr double kLn2 = 0.69314718055994530942;
 
 enum : int {
   kOK = 0, kE_ARG = 1, kE_UNSORTED = 2, kE_ID_RANGE = 3, kE_TIME_RANGE = 4,
-  kE_NONFINITE = 5, kE_MAXITER = 6
+  kE_NONFINITE = 5, kE_MAXITER = 6, kE_TIMEOUT = 7
 };
 
 // private accumulators for template capacity M (atomics beyond)
@@ -129,7 +129,7 @@ __device__ __forceinline__ int chunk_begin(int c, int NC, int N, const EV &ev) {
 struct Carve {
   // byte offsets
   int alpha, oh, ga, mu, gm, beta, bl2, gb, W, cnt, C, dC, endR, endS, anc, bnd, encR, encS, prev,
-      gbuf, am, av, red, ctl, gpriv, mpriv, ev_t, ev_u, ev_w, tstart, tf, tl, P, xs;
+      gbuf, am, av, red, ctl, gpriv, mpriv, ev_t, ev_u, ev_w, tstart, tf, tl, P, xs, ring, mbar;
   int total;
 };
 
@@ -182,7 +182,8 @@ __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, 
 // per-thread segment sums, (NT + M) slots of M + 4 floats (the chunk/type
 // counters of the feature pass share the same space); xcap > 0 places the
 // features in shared memory (xcap events x M floats).
-__host__ __device__ inline Carve make_carve_x(int M, int NT, int xcap, bool adam) {
+__host__ __device__ inline Carve make_carve_x(int M, int NT, int xcap, bool adam,
+                                              int pipe_steps = 0, int pipe_stages = 0) {
   Carve c = {};
   int o = 0;
   const int AP = pitch4(M);
@@ -216,6 +217,11 @@ __host__ __device__ inline Carve make_carve_x(int M, int NT, int xcap, bool adam
   c.tl = take(M * 4);
   c.P = take((NT + M) * (M + 4) * 4);
   c.xs = xcap > 0 ? take(xcap * M * 4) : 0;
+  // streamed features: a ring of pipe_stages buffers of pipe_steps steps
+  // (NT float4 per slice and step) filled by bulk copies, one mbarrier each
+  const bool pipe = xcap == 0 && pipe_stages > 0 && pipe_steps > 0;
+  c.mbar = pipe ? take(pipe_stages * 8) : 0;
+  c.ring = pipe ? take(pipe_stages * pipe_steps * (M / 4) * NT * 16) : 0;
   c.total = o;
   return c;
 }
@@ -227,7 +233,8 @@ struct Sm {
       *encS, *prev, *gbuf, *am, *av, *gpriv, *mpriv;
   int *bnd, *cnt, *ctl, *tstart, *tf, *tl;
   float *P;
-  float4 *xs;
+  float4 *xs, *ring;
+  uint64_t *mbar;
   double *red;
   float *ev_t, *ev_w;
   uint16_t *ev_u;
@@ -247,6 +254,7 @@ struct Sm {
     ev_u = (uint16_t *)(base + c.ev_u);
     tstart = (int *)(base + c.tstart); tf = (int *)(base + c.tf); tl = (int *)(base + c.tl);
     P = (float *)(base + c.P); xs = (float4 *)(base + c.xs);
+    ring = (float4 *)(base + c.ring); mbar = (uint64_t *)(base + c.mbar);
   }
 };
 
