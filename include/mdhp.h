@@ -190,6 +190,11 @@ mdhp_status mdhp_fit_batch(mdhp_plan *plan, const mdhp_batch *batch, const mdhp_
 mdhp_status mdhp_plan_set_timing(mdhp_plan *plan, int32_t enable);
 float mdhp_plan_last_fit_ms(mdhp_plan *plan);
 
+/* Number of kernels the last mdhp_fit_batch on this plan launched (length
+ * keys, the radix sort counted as one kernel, the range split, the fit
+ * kernels; not the learned initializer's), or -1 for a NULL plan. */
+int32_t mdhp_plan_last_launches(const mdhp_plan *plan);
+
 /* Launch shape (for tests, reports and tuning): threads per window and
  * threads per chunk of the event recursion, and the shared-memory cutoff:
  * windows of at most this many events are staged in shared memory (the
@@ -207,16 +212,19 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
  * with `opts` for each candidate launch shape and keeps the fastest in the
  * plan.  Candidates: 64, 128 and 256 threads per window; for the decoupled
  * fixed-beta kernels the shared-memory class (none, half, the largest that
- * fits) and the feature ring (none; 1x4, 2x3, 2x4, 4x3 steps x stages); for
- * the event recursion every built threads-per-chunk split and the
+ * fits), the feature ring (none; 1x4, 2x3, 2x4, 4x3 steps x stages) and the
+ * two-launch split (off; 256 x 1, 128 x 1, 128 x 2 long threads x CTAs per
+ * SM); for the event recursion every built threads-per-chunk split and the
  * staging cutoff (none, the default, the largest that fits).  Each candidate
  * runs tune_iters iterations (<= 0: 20) with tol = 0 after one warm-up run.
  *   mu, alpha, beta  device, as for mdhp_fit_batch; used as the starting point
  *                    when opts->init == 0 and restored on return
  *   loglik, iters, win_status  device scratch, overwritten
- *   chosen   int32[6] host or NULL: path (0 decoupled, 1 recursion), threads
- *            per window, threads per chunk (0 for decoupled), cutoff, and the
- *            feature ring's steps per stage and stages (mdhp_plan_set_pipeline)
+ *   chosen   int32[9] host or NULL: path (0 decoupled, 1 recursion), threads
+ *            per window, threads per chunk (0 for decoupled), cutoff, the
+ *            feature ring's steps per stage and stages (mdhp_plan_set_pipeline),
+ *            and the split (enabled, long_threads, long_ctas_per_sm;
+ *            mdhp_plan_set_split)
  *   best_ms  float host or NULL: device time of the chosen shape
  * When the plan was created with an autotune_cache path, the choice is
  * written there under a key of the device name and compute capability, M,
@@ -322,6 +330,23 @@ mdhp_status mdhp_plan_set_path(mdhp_plan *plan, int32_t path);
 mdhp_status mdhp_plan_set_pipeline(mdhp_plan *plan, int32_t steps_per_stage, int32_t stages);
 mdhp_status mdhp_plan_get_pipeline(const mdhp_plan *plan, int32_t *steps_per_stage,
                                    int32_t *stages);
+
+/* Split of the decoupled kernels' streamed windows over two concurrent
+ * launches that share one length-sorted queue from its two ends: the longest
+ * windows are taken from the front by CTAs of long_threads threads
+ * (long_ctas_per_sm per SM), the shortest from the back by CTAs of the plan's
+ * threads per window, as many per SM as the rest of the SM holds; the two
+ * meet in the middle, so neither needs a split point.  Fewer, wider CTAs on
+ * the long windows keep fewer windows' features in flight (they then stay in
+ * L2).  Used when the threads per window differ from long_threads and no
+ * shared-memory feature class is set.  Default: enabled, 256 threads, 1 per
+ * SM.  long_threads 64, 128 or 256; long_ctas_per_sm 1..8.  Results do not
+ * depend on the split (each window is fitted by one CTA either way, with the
+ * summation order of its block size). */
+mdhp_status mdhp_plan_set_split(mdhp_plan *plan, int32_t enable, int32_t long_threads,
+                                int32_t long_ctas_per_sm);
+mdhp_status mdhp_plan_get_split(const mdhp_plan *plan, int32_t *enable, int32_t *long_threads,
+                                int32_t *long_ctas_per_sm);
 
 /*
  * Batched fit without a plan and without allocating device memory.  (An

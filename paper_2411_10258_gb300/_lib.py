@@ -56,6 +56,9 @@ SIGNATURES = [
                                           P, P, P, P, P, P, ctypes.c_int32, P, P, P]),
     ("mdhp_plan_set_pipeline", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32]),
     ("mdhp_plan_get_pipeline", ctypes.c_int, [P, P, P]),
+    ("mdhp_plan_set_split", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    ("mdhp_plan_get_split", ctypes.c_int, [P, P, P, P]),
+    ("mdhp_plan_last_launches", ctypes.c_int32, [P]),
     ("mdhp_simulate", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P,
                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P, P]),
     ("mdhp_init_model_create", ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32,

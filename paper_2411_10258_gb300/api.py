@@ -185,6 +185,10 @@ class Plan:
     def last_fit_ms(self) -> float:
         return float(self.lib.mdhp_plan_last_fit_ms(self.h))
 
+    def last_launches(self) -> int:
+        """Kernels launched by the last fit (mdhp_plan_last_launches)."""
+        return int(self.lib.mdhp_plan_last_launches(self.h))
+
     def shape(self):
         v = [ctypes.c_int32() for _ in range(3)]
         _lib.check(self.lib.mdhp_plan_get_shape(self.h, *[ctypes.byref(x) for x in v]), "get_shape")
@@ -211,7 +215,7 @@ class Plan:
         scratch = dict(loglik=torch.empty(B, dtype=torch.float64, device=dev),
                        iters=torch.empty(B, dtype=torch.int32, device=dev),
                        status=torch.empty(B, dtype=torch.int32, device=dev))
-        chosen = (ctypes.c_int32 * 6)()
+        chosen = (ctypes.c_int32 * 9)()
         best = ctypes.c_float(-1.0)
         st = db.c_struct()
         o = opts.c_struct()
@@ -222,12 +226,24 @@ class Plan:
         _lib.check(rc, "mdhp_plan_autotune")
         return dict(path=("decoupled", "recursion")[chosen[0]], threads_per_window=chosen[1],
                     threads_per_chunk=chosen[2], cutoff=chosen[3], pipe_steps=chosen[4],
-                    pipe_stages=chosen[5], ms=best.value)
+                    pipe_stages=chosen[5], split=bool(chosen[6]), split_threads=chosen[7],
+                    split_ctas=chosen[8], ms=best.value)
 
     def set_pipeline(self, steps_per_stage: int, stages: int):
         """Feature ring of the decoupled kernels (mdhp_plan_set_pipeline); stages=0: none."""
         _lib.check(self.lib.mdhp_plan_set_pipeline(self.h, steps_per_stage, stages),
                    "mdhp_plan_set_pipeline")
+
+    def set_split(self, enable: bool, long_threads: int = 256, long_ctas_per_sm: int = 1):
+        """Two launches over one queue (mdhp_plan_set_split)."""
+        _lib.check(self.lib.mdhp_plan_set_split(self.h, 1 if enable else 0, long_threads,
+                                                long_ctas_per_sm), "mdhp_plan_set_split")
+
+    def split(self):
+        v = [ctypes.c_int32() for _ in range(3)]
+        _lib.check(self.lib.mdhp_plan_get_split(self.h, *[ctypes.byref(x) for x in v]),
+                   "mdhp_plan_get_split")
+        return (bool(v[0].value), v[1].value, v[2].value)
 
     def pipeline(self):
         v = [ctypes.c_int32() for _ in range(2)]

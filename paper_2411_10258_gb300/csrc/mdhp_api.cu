@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <utility>
 #include <vector>
@@ -158,7 +159,8 @@ struct mdhp_plan {
   int64_t max_events;
   Shape shape;
   int *keys = nullptr, *keys_sorted = nullptr, *idx = nullptr, *order = nullptr;
-  int *ctl = nullptr;  // [0] queue long, [1] queue short, [2..3] range long, [4..5] range short
+  int *ctl = nullptr;  // [0] queue long, [1] queue short, [2..3] range long, [4..5] range short,
+                       // [6..8] two-ended queue (claimed, front, back)
   void *sort_tmp = nullptr;
   size_t sort_tmp_bytes = 0;
   cudaStream_t side = nullptr;
@@ -173,8 +175,15 @@ struct mdhp_plan {
   // streamed features of the decoupled kernels: ring of pipe_stages shared-memory
   // buffers of pipe_steps steps filled by bulk copies (0 stages: register prefetch)
   int pipe_steps = 0, pipe_stages = 0;  // measured: register prefetch is faster on the bench workloads
+  // two concurrent launches over one length-sorted queue: the longest windows
+  // from the front with xnt_long threads (xcta_long CTAs per SM), the
+  // shortest from the back with xnt threads, as many CTAs per SM as the rest
+  // of the register file holds; fewer windows in flight keeps their features
+  // in L2.  0 = one launch of xnt threads.
+  int xdual = 1, xnt_long = 256, xcta_long = 1;
   mdhp_init_model *model = nullptr;  // learned initializer (not owned)
   std::string cache;                 // autotune cache file ("" = none)
+  int launches = 0;                  // kernel launches of the last mdhp_fit_batch
 };
 
 // --- autotuner: cache of tuned launch shapes ---------------------------------
@@ -183,7 +192,8 @@ struct mdhp_plan {
 //   {"format": "mdhp-autotune-1", "entries": [
 //   {"key": "<device>|sm<cc>|M<M>|mode<m>|W<max_windows>|E<max_events>|<path>",
 //    "threads_per_window": 64, "threads_per_chunk": 0, "smem_cutoff_events": 0,
-//    "pipe_steps": 2, "pipe_stages": 3, "ms": 14.8},
+//    "pipe_steps": 0, "pipe_stages": 0, "split": 1, "split_threads": 256, "split_ctas": 1,
+//    "ms": 10.3},
 //   ...]}
 // keyed by the device and the plan's creation arguments; <path> is "decoupled"
 // (fixed-beta features kernels: threads per window and the shared-memory
@@ -297,6 +307,14 @@ void tune_load(mdhp_plan *p) {
           p->pipe_stages = pd;
           p->pipe_steps = pd > 0 ? ps : 0;
         }
+        const int du = field_int(e.second, "split", p->xdual);
+        const int ntl = field_int(e.second, "split_threads", p->xnt_long);
+        const int cl = field_int(e.second, "split_ctas", p->xcta_long);
+        if ((ntl == 64 || ntl == 128 || ntl == 256) && cl >= 1 && cl <= 8) {
+          p->xdual = du ? 1 : 0;
+          p->xnt_long = ntl;
+          p->xcta_long = cl;
+        }
       }
       if (path == 1) apply_recursion(p, nt, spl, cut);
     }
@@ -304,8 +322,11 @@ void tune_load(mdhp_plan *p) {
   cudaGetLastError();
 }
 
-bool tune_store(const mdhp_plan *p, int path, int nt, int spl, int cutoff, int ps, int pd,
-                float ms) {
+struct TuneChoice {
+  int nt, spl, cut, ps, pd, dual, ntl, cl;
+};
+
+bool tune_store(const mdhp_plan *p, int path, const TuneChoice &c, float ms) {
   if (p->cache.empty()) return true;
   std::string text;
   read_text(p->cache, text);
@@ -314,8 +335,9 @@ bool tune_store(const mdhp_plan *p, int path, int nt, int spl, int cutoff, int p
   char line[768];
   snprintf(line, sizeof(line),
            "{\"key\": \"%s\", \"threads_per_window\": %d, \"threads_per_chunk\": %d, "
-           "\"smem_cutoff_events\": %d, \"pipe_steps\": %d, \"pipe_stages\": %d, \"ms\": %.4f}",
-           key.c_str(), nt, spl, cutoff, ps, pd, ms);
+           "\"smem_cutoff_events\": %d, \"pipe_steps\": %d, \"pipe_stages\": %d, "
+           "\"split\": %d, \"split_threads\": %d, \"split_ctas\": %d, \"ms\": %.4f}",
+           key.c_str(), c.nt, c.spl, c.cut, c.ps, c.pd, c.dual, c.ntl, c.cl, ms);
   bool found = false;
   for (auto &e : v)
     if (e.first == key) {
@@ -331,6 +353,70 @@ bool tune_store(const mdhp_plan *p, int path, int nt, int spl, int cutoff, int p
   fprintf(f, "]}\n");
   const bool ok = fclose(f) == 0;
   return ok && rename(tmp.c_str(), p->cache.c_str()) == 0;
+}
+
+// The two-launch decoupled fit (plan field xdual): both launches share the
+// sorted range ctl[2..3] through the two-ended queue ctl[6..8].  *done is
+// false (and nothing is launched) when the shapes do not fit together.
+mdhp_status launch_dual(mdhp_plan *p, const FitArgs &ax, bool adam, cudaStream_t st, bool *done) {
+  *done = false;
+  const int ntL = p->xnt_long, ntS = p->xnt;
+  FitFn fL = get_fitx(p->Mt, p->beta_mode, XM_GLOBAL, ntL);
+  FitFn fS = get_fitx(p->Mt, p->beta_mode, XM_GLOBAL, ntS);
+  if (!fL || !fS || ntL < p->Mt) return MDHP_OK;
+  FitArgs aL = ax, aS = ax;
+  aL.range = aS.range = p->ctl + 2;
+  aL.dq = aS.dq = p->ctl + 6;
+  aL.ev_cap = aS.ev_cap = p->xcap;
+  aL.pipe_stages = aS.pipe_stages = 0;
+  aL.qdir = 1;
+  aS.qdir = 2;
+  aL.carve = make_carve_x(p->Mt, ntL, 0, adam);
+  aS.carve = make_carve_x(p->Mt, ntS, 0, adam);
+  mdhp_status s;
+  if ((s = prepare_kernel((const void *)fL, aL.carve.total)) != MDHP_OK) return s;
+  if ((s = prepare_kernel((const void *)fS, aS.carve.total)) != MDHP_OK) return s;
+  // CTAs per SM: the long class as configured (at most its occupancy); the
+  // short class what the long one leaves of the registers, shared memory and
+  // thread slots
+  int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaFuncAttributes faL{}, faS{};
+  if (cudaFuncGetAttributes(&faL, fL) != cudaSuccess || cudaFuncGetAttributes(&faS, fS) != cudaSuccess) {
+    cudaGetLastError();
+    return MDHP_OK;
+  }
+  int occL = 0, occS = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occL, fL, ntL, aL.carve.total);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occS, fS, ntS, aS.carve.total);
+  const int cL = std::min(p->xcta_long, occL);
+  if (cL < 1) return MDHP_OK;
+  const int rL = (faL.numRegs + 7) / 8 * 8, rS = (faS.numRegs + 7) / 8 * 8;
+  int cS = (regs_sm - cL * ntL * rL) / (ntS * rS);
+  cS = std::min(cS, (smem_sm - cL * (aL.carve.total + 1024)) / (aS.carve.total + 1024));
+  cS = std::min(cS, (thr_sm - cL * ntL) / ntS);
+  cS = std::min(cS, occS);
+  if (cS < 1) return MDHP_OK;
+  const int gL = num_sms() * cL;
+  int gS = num_sms() * cS;
+  if (gL + gS > p->xgrid) gS = p->xgrid - gL;
+  if (gS < 1) return MDHP_OK;
+  aL.slot_base = 0;
+  aS.slot_base = gL;
+  cudaEventRecord(p->ev_fork, st);
+  cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+  fL<<<gL, ntL, aL.carve.total, p->side>>>(aL);
+  if ((s = cuda_check("k_fit_x (long windows, front of the queue)")) != MDHP_OK) return s;
+  cudaEventRecord(p->ev_join, p->side);
+  fS<<<gS, ntS, aS.carve.total, st>>>(aS);
+  p->launches += 2;
+  if ((s = cuda_check("k_fit_x (short windows, back of the queue)")) != MDHP_OK) return s;
+  cudaStreamWaitEvent(st, p->ev_join, 0);
+  *done = true;
+  return MDHP_OK;
 }
 
 }  // namespace
@@ -438,6 +524,9 @@ __global__ void k_split(const int *keys_sorted, int B, int cutoff, int has_long,
     ctl[3] = lo;
     ctl[4] = lo;
     ctl[5] = B;
+    ctl[6] = 0;  // two-ended queue: claimed, taken from the front, taken from the back
+    ctl[7] = 0;
+    ctl[8] = 0;
   }
 }
 
@@ -464,7 +553,7 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
   ok &= cudaMalloc(&p->keys_sorted, sizeof(int) * max_windows) == cudaSuccess;
   ok &= cudaMalloc(&p->idx, sizeof(int) * max_windows) == cudaSuccess;
   ok &= cudaMalloc(&p->order, sizeof(int) * max_windows) == cudaSuccess;
-  ok &= cudaMalloc(&p->ctl, sizeof(int) * 8) == cudaSuccess;
+  ok &= cudaMalloc(&p->ctl, sizeof(int) * 16) == cudaSuccess;
   if (ok) {
     cub::DeviceRadixSort::SortPairsDescending(nullptr, p->sort_tmp_bytes, p->keys, p->keys_sorted,
                                               p->idx, p->order, max_windows);
@@ -591,6 +680,32 @@ mdhp_status mdhp_plan_set_pipeline(mdhp_plan *p, int32_t steps_per_stage, int32_
   return MDHP_OK;
 }
 
+int32_t mdhp_plan_last_launches(const mdhp_plan *p) { return p ? p->launches : -1; }
+
+mdhp_status mdhp_plan_set_split(mdhp_plan *p, int32_t enable, int32_t long_threads,
+                                int32_t long_ctas_per_sm) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  if (enable) {
+    if (long_threads != 64 && long_threads != 128 && long_threads != 256)
+      return fail(MDHP_E_ARG, "long_threads %d (64, 128 or 256)", long_threads);
+    if (long_ctas_per_sm < 1 || long_ctas_per_sm > 8)
+      return fail(MDHP_E_ARG, "long_ctas_per_sm %d (1..8)", long_ctas_per_sm);
+    p->xnt_long = long_threads;
+    p->xcta_long = long_ctas_per_sm;
+  }
+  p->xdual = enable ? 1 : 0;
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_plan_get_split(const mdhp_plan *p, int32_t *enable, int32_t *long_threads,
+                                int32_t *long_ctas_per_sm) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  if (enable) *enable = p->xdual;
+  if (long_threads) *long_threads = p->xnt_long;
+  if (long_ctas_per_sm) *long_ctas_per_sm = p->xcta_long;
+  return MDHP_OK;
+}
+
 mdhp_status mdhp_plan_get_pipeline(const mdhp_plan *p, int32_t *steps_per_stage, int32_t *stages) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
   if (steps_per_stage) *steps_per_stage = p->pipe_steps;
@@ -663,6 +778,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   int ev_cap = (bound > 0 && bound < sh.cutoff) ? (int)bound : sh.cutoff;
   const bool need_long = !(bound > 0 && bound <= sh.cutoff);
 
+  p->launches = 3;  // k_lengths, the radix sort (one kernel at these sizes), k_split
   k_lengths<<<(B + 255) / 256, 256, 0, st>>>(batch->offsets, B, p->keys, p->idx);
   if ((s = cuda_check("k_lengths")) != MDHP_OK) return s;
   size_t tmp = p->sort_tmp_bytes;
@@ -707,7 +823,11 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     ax.xbuf = p->xbuf;
     const bool any_long = !(xres > 0 && bound <= xres);
     if (p->timing && !t0_done) cudaEventRecord(p->ev_t0, st);
-    if (any_long) {
+    bool dual_done = false;
+    if (any_long && xres == 0 && p->xdual && p->xnt_long != p->xnt) {
+      if ((s = launch_dual(p, ax, o->optimizer == 1, st, &dual_done)) != MDHP_OK) return s;
+    }
+    if (any_long && !dual_done) {
       FitArgs al = ax;
       al.queue = p->ctl + 0;
       al.range = p->ctl + 2;
@@ -732,6 +852,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
       int gl = num_sms() * (occ > 0 ? occ : 1);
       if (gl > p->xgrid) gl = p->xgrid;
       fx<<<gl, p->xnt, al.carve.total, ls>>>(al);
+      ++p->launches;
       if ((s = cuda_check("k_fit_x (global features)")) != MDHP_OK) return s;
       if (xres > 0) cudaEventRecord(p->ev_join, p->side);
     }
@@ -748,6 +869,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
       int grid = num_sms() * (occr > 0 ? occr : 1);
       if (grid > B) grid = B;
       fr<<<grid, p->xnt, ar.carve.total, st>>>(ar);
+      ++p->launches;
       if ((s = cuda_check("k_fit_x (shared features)")) != MDHP_OK) return s;
       if (any_long) cudaStreamWaitEvent(st, p->ev_join, 0);
     }
@@ -772,6 +894,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fl, sh.nt, al.carve.total);
     const int grid = num_sms() * (occ > 0 ? occ : 1);
     fl<<<grid, sh.nt, al.carve.total, st>>>(al);
+    ++p->launches;
     if ((s = cuda_check("k_fit (streamed)")) != MDHP_OK) return s;
   }
   {
@@ -791,6 +914,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     int grid = num_sms() * (occ > 0 ? occ : 1);
     if (grid > B) grid = B;
     fs<<<grid, sh.nt, as.carve.total, st>>>(as);
+    ++p->launches;
     if ((s = cuda_check("k_fit (staged)")) != MDHP_OK) return s;
   }
   if (p->timing) {
@@ -844,7 +968,7 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
     }
   };
   copy_params(true);
-  struct Cand { int nt, spl, cut, ps, pd; };
+  using Cand = TuneChoice;
   std::vector<Cand> cands;
   static const int kPipes[][2] = {{0, 0}, {1, 4}, {2, 3}, {2, 4}, {4, 3}};
   for (int nt = 64; nt <= 256; nt *= 2) {
@@ -853,10 +977,13 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
       const int fit = xres_fit(p, nt, adam);
       for (const auto &pd : kPipes) {
         if (pd[1] > 0 && make_carve_x(p->Mt, nt, 0, adam, pd[0], pd[1]).total > max_dyn_smem()) continue;
-        cands.push_back({nt, 0, 0, pd[0], pd[1]});
-        if (fit >= 64) cands.push_back({nt, 0, fit, pd[0], pd[1]});
+        cands.push_back({nt, 0, 0, pd[0], pd[1], 0, 256, 1});
+        if (fit >= 64) cands.push_back({nt, 0, fit, pd[0], pd[1], 0, 256, 1});
       }
-      if (fit >= 128) cands.push_back({nt, 0, fit / 2 / 32 * 32, p->pipe_steps, p->pipe_stages});
+      if (fit >= 128) cands.push_back({nt, 0, fit / 2 / 32 * 32, 0, 0, 0, 256, 1});
+      static const int kSplits[][2] = {{256, 1}, {128, 1}, {128, 2}};
+      for (const auto &sp : kSplits)
+        if (sp[0] != nt && nt < 256) cands.push_back({nt, 0, 0, 0, 0, 1, sp[0], sp[1]});
     } else {
       for (int spl = 1; spl <= 32; spl *= 2) {
         if (nt % spl || !get_fit(p->Mt, spl, p->beta_mode, learn, true) ||
@@ -864,9 +991,9 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
           continue;
         const int fit = stage_fit(p, nt, spl, batch->weights != nullptr, learn, adam);
         const int dflt = default_shape(p->Mt).cutoff;
-        cands.push_back({nt, spl, 0, p->pipe_steps, p->pipe_stages});
-        if (dflt <= fit) cands.push_back({nt, spl, dflt, p->pipe_steps, p->pipe_stages});
-        if (fit >= 64 && fit != dflt) cands.push_back({nt, spl, fit, p->pipe_steps, p->pipe_stages});
+        cands.push_back({nt, spl, 0, 0, 0, 0, 256, 1});
+        if (dflt <= fit) cands.push_back({nt, spl, dflt, 0, 0, 0, 256, 1});
+        if (fit >= 64 && fit != dflt) cands.push_back({nt, spl, fit, 0, 0, 0, 256, 1});
       }
     }
   }
@@ -879,17 +1006,23 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
   const Shape shape0 = p->shape;
   const int xnt0 = p->xnt, xres0 = p->xres, timing0 = p->timing;
   const int ps0 = p->pipe_steps, pd0 = p->pipe_stages;
+  const int du0 = p->xdual, ntl0 = p->xnt_long, cl0 = p->xcta_long;
   p->timing = 0;
   float best = -1.f;
-  Cand win{0, 0, 0, 0, 0};
+  Cand win{0, 0, 0, 0, 0, 0, 256, 1};
   mdhp_status last = MDHP_OK;
   for (size_t c = 0; c <= cands.size(); ++c) {
     const Cand cd = cands[c == 0 ? 0 : c - 1];  // run 0 warms the first candidate up
     const bool okc = path == 0 ? apply_decoupled(p, cd.nt, cd.cut)
                                : apply_recursion(p, cd.nt, cd.spl, cd.cut);
     if (!okc) continue;
-    p->pipe_steps = cd.ps;
-    p->pipe_stages = cd.pd;
+    if (path == 0) {
+      p->pipe_steps = cd.ps;
+      p->pipe_stages = cd.pd;
+      p->xdual = cd.dual;
+      p->xnt_long = cd.ntl;
+      p->xcta_long = cd.cl;
+    }
     copy_params(false);
     cudaEventRecord(e0, st);
     const mdhp_status r = mdhp_fit_batch(p, batch, &oo, mu, alpha, beta, loglik, iters, win_status, stream);
@@ -916,6 +1049,9 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
   p->xres = xres0;
   p->pipe_steps = ps0;
   p->pipe_stages = pd0;
+  p->xdual = du0;
+  p->xnt_long = ntl0;
+  p->xcta_long = cl0;
   copy_params(false);
   cudaStreamSynchronize(st);
   cudaFree(snap);
@@ -927,6 +1063,9 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
     apply_decoupled(p, win.nt, win.cut);
     p->pipe_steps = win.ps;
     p->pipe_stages = win.pd;
+    p->xdual = win.dual;
+    p->xnt_long = win.ntl;
+    p->xcta_long = win.cl;
   } else {
     apply_recursion(p, win.nt, win.spl, win.cut);
   }
@@ -937,9 +1076,12 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
     chosen[3] = win.cut;
     chosen[4] = path == 0 ? win.ps : 0;
     chosen[5] = path == 0 ? win.pd : 0;
+    chosen[6] = path == 0 ? win.dual : 0;
+    chosen[7] = path == 0 ? win.ntl : 0;
+    chosen[8] = path == 0 ? win.cl : 0;
   }
   if (best_ms) *best_ms = best;
-  if (!tune_store(p, path, win.nt, win.spl, win.cut, win.ps, win.pd, best))
+  if (!tune_store(p, path, win, best))
     return fail(MDHP_E_ARG, "autotune: cannot write the cache file %s", p->cache.c_str());
   return MDHP_OK;
 }

@@ -309,8 +309,10 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
   const int nupd = Mrt + Mrt * Mrt;
   const int tid = threadIdx.x, NT = NTC > 0 ? NTC : (int)blockDim.x;
   const int xcap = a.ev_cap;
-  // global slot: (xcap + 2 NT) rows, enough for L * NT with the odd rounding of L
-  float4 *Xg = XS ? nullptr : a.xbuf + (size_t)blockIdx.x * (M / 4) * (size_t)(xcap + 2 * NT);
+  // global slot: (xcap + 512) rows, enough for L * NT with the odd rounding of
+  // L for every block size up to 256 (one stride for all launches of a plan)
+  float4 *Xg = XS ? nullptr
+                  : a.xbuf + (size_t)(a.slot_base + blockIdx.x) * (M / 4) * (size_t)(xcap + 512);
   constexpr bool pipe = XM == XM_RING;
   XPipe pp{Xg, (M / 4) * NT, 1, a.pipe_steps, a.pipe_stages, 1, 0u, 0u, 0u};
   if (pipe) {
@@ -321,14 +323,23 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     __syncthreads();
   }
   for (;;) {
-    if (tid == 0) sm.ctl[1] = atomicAdd(a.queue, 1);
+    if (tid == 0) {
+      const int qb = a.range ? a.range[0] : a.qbegin;
+      const int qe = a.range ? a.range[1] : a.qend;
+      int pos = -1;
+      if (a.qdir == 0) {
+        const int q = atomicAdd(a.queue, 1);
+        pos = qb + q < qe ? qb + q : -1;
+      } else if (atomicAdd(a.dq, 1) < qe - qb) {  // a window is left: take it from this end
+        pos = a.qdir == 1 ? qb + atomicAdd(a.dq + 1, 1) : qe - 1 - atomicAdd(a.dq + 2, 1);
+      }
+      sm.ctl[1] = pos;
+    }
     __syncthreads();
-    const int q = sm.ctl[1];
-    const int qb = a.range ? a.range[0] : a.qbegin;
-    const int qe = a.range ? a.range[1] : a.qend;
+    const int pos = sm.ctl[1];
     __syncthreads();
-    if (qb + q >= qe) break;
-    const int b = a.order ? a.order[qb + q] : qb + q;
+    if (pos < 0) break;
+    const int b = a.order ? a.order[pos] : pos;
     const int64_t o0 = a.offsets[b];
     const int N = (int)(a.offsets[b + 1] - o0);
     const float T = a.T[b];

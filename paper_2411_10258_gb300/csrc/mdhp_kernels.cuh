@@ -41,6 +41,12 @@ struct FitArgs {
   double tol;
   float4 *xbuf;  // decoupled fit: per-CTA feature scratch (global), or nullptr
   int pipe_steps, pipe_stages;  // streamed features: bulk-copy ring (0 stages: register prefetch)
+  // decoupled fit, two launches sharing one length-sorted range: qdir 1 takes
+  // windows from the front (longest first), qdir 2 from the back; dq =
+  // {claimed, front, back} counters; 0 = the single-ended queue `queue`
+  int qdir;
+  int *dq;
+  int slot_base;  // first feature-scratch slot of this launch
   Carve carve;
 };
 
