@@ -171,7 +171,9 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
   if (FIXED) to_decays<M, SPL>(a.NC, sm);
   const float invN = 1.f / (float)max(N, 1);
   // convergence bookkeeping lives in thread 0; decisions go through ctl[2]
-  double lnl_prev = 0.0, lnl_out = 0.0;
+  FF lnl_prev{0.f, 0.f}, lnl_out{0.f, 0.f};
+  const bool use_tol = a.tol > 0.0;
+  const float tolf = (float)a.tol;
   int streak = 0, k = 0;
   int wst = a.tol > 0.0 ? kE_MAXITER : kOK;
   float b1t = 1.f, b2t = 1.f;
@@ -180,15 +182,15 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
     evaluate<M, SPL, BM, LEARN, FIXED>(a.NC, ev, T, Mrt, sm, nullptr);
     int bad = 0;
     if (tid == 0) {
-      const double val = lnl_total(sm);
-      bad = !isfinite(val);
+      const FF val = lnl_total_ff(sm);
+      bad = !isfinite(val.hi);
       int decision = 0;  // 0 update, 1 stop
       if (!bad) {
-        if (k > 0 && a.tol > 0.0 && fabs(val - lnl_prev) <= a.tol * fabs(val)) ++streak;
+        if (k > 0 && use_tol && ff_small_change(val, lnl_prev, tolf)) ++streak;
         else streak = 0;
         lnl_prev = val;
         lnl_out = val;
-        if (a.tol > 0.0 && streak >= a.patience) { wst = kOK; decision = 1; }
+        if (use_tol && streak >= a.patience) { wst = kOK; decision = 1; }
         else if (k == a.max_iters - 1) decision = 1;
       } else if (k == 0) {
         lnl_out = val;
@@ -243,7 +245,7 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
   for (int i = tid; i < Mrt; i += blockDim.x) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];
   for (int j = tid; j < nb; j += blockDim.x) a.beta[(int64_t)b * nb + j] = sm.beta[j];
   if (tid == 0) {
-    a.loglik[b] = lnl_out;
+    a.loglik[b] = ff_to_double(lnl_out);
     a.iters[b] = k;
     a.status[b] = wst;
   }

@@ -83,6 +83,41 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   s = t;
 }
 
+// Double-float numbers (hi + lo, about 48 significant bits) for the lnL total,
+// the convergence test and the compensator constants of every iteration: on
+// GB300 a dependent FP64 add takes about 64 cycles (FP32: 4.5) and a
+// float<->double conversion about 50, which put FP64 arithmetic on every
+// iteration's critical path.  TwoSum
+// (Knuth) for additions, an FMA-based exact product for the scaling by ln 2;
+// the result goes to FP64 once, when the window is done.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_norm(float s, float e) {
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+  return ff_norm(s, e);
+}
+__device__ __forceinline__ FF ff_mul(FF a, float bh, float bl) {
+  const float p = a.hi * bh;
+  const float e = fmaf(a.hi, bh, -p) + fmaf(a.hi, bl, a.lo * bh);
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ FF ff_div(FF a, float b) {
+  const float q = a.hi / b;
+  const float r = fmaf(-q, b, a.hi) + a.lo;
+  return ff_norm(q, r / b);
+}
+__device__ __forceinline__ double ff_to_double(FF v) { return (double)v.hi + (double)v.lo; }
+constexpr float kLn2Hi = 0.693147182464599609375f;  // the float nearest ln 2
+constexpr float kLn2Lo = -1.9046542999e-09f;          // ln 2 - kLn2Hi
+
+
 // ---------------------------------------------------------------------------
 // Event access: staged in shared memory (t float, id uint16: 6 bytes per
 // event) or read from global memory.
@@ -506,8 +541,13 @@ __device__ int stage_and_validate(const float *tg, const int16_t *ug, const floa
   }
   if (code != 0x7fffffff) atomicMin(&sm.ctl[0], code);
   __syncthreads();
-  if (!wg)
-    for (int j = tid; j < M; j += nt) sm.W[j] = (double)sm.cnt[j];
+  // W_j becomes a double-float in place (the same 8 bytes), so the compensator
+  // constants of every iteration need no FP64 arithmetic
+  for (int j = tid; j < M; j += nt) {
+    const double w = wg ? sm.W[j] : (double)sm.cnt[j];
+    const float hi = (float)w;
+    reinterpret_cast<float2 *>(sm.W)[j] = make_float2(hi, (float)(w - (double)hi));
+  }
   __syncthreads();
   const int st = sm.ctl[0];
   return st == 0x7fffffff ? kOK : st;
@@ -545,10 +585,18 @@ __device__ void prepare_states(int NC, const EV &ev, int Mrt, Sm<M> &sm) {
   __syncthreads();
   for (int j = tid; j < M; j += blockDim.x) {
     if (j < Mrt) {
-      const double b = (double)sm.beta[BM == 0 ? 0 : j];
-      const double Cj = (sm.W[j] - (double)sm.endR[j]) / b;
-      sm.C[j] = (float)Cj;
-      sm.dC[j] = LEARN ? (float)(((double)sm.endS[j] - Cj) / b) : 0.f;
+      // C_j = (W_j - R_j(T)) / beta_j and dC_j = (S_j(T) - C_j) / beta_j in
+      // double-float: W_j - R_j(T) cancels for windows that end on a burst
+      const float b = sm.beta[BM == 0 ? 0 : j];
+      const float2 w = reinterpret_cast<const float2 *>(sm.W)[j];
+      const FF Cj = ff_div(ff_add(FF{w.x, w.y}, FF{-sm.endR[j], 0.f}), b);
+      sm.C[j] = Cj.hi + Cj.lo;
+      if (LEARN) {
+        const FF e = ff_add(FF{sm.endS[j], 0.f}, FF{-Cj.hi, -Cj.lo});
+        sm.dC[j] = (e.hi + e.lo) / b;
+      } else {
+        sm.dC[j] = 0.f;
+      }
     } else {
       sm.C[j] = 0.f;
       sm.dC[j] = 0.f;
@@ -745,6 +793,26 @@ __device__ void evaluate(int NC, const EV &ev, float T, int Mrt, Sm<M> &sm, floa
 }
 
 // lnL from the per-warp partials (FP64: the only double arithmetic per evaluation).
+// lnL from the per-warp partials (Part1 in log2 units, Part2+3) as a double-float.
+template <int M>
+__device__ __forceinline__ FF lnl_total_ff(const Sm<M> &sm) {
+  const int nw = (blockDim.x + 31) >> 5;
+  const float4 *r4 = reinterpret_cast<const float4 *>(sm.red);
+  FF p1{0.f, 0.f}, p23{0.f, 0.f};
+  for (int w = 0; w < nw; ++w) {
+    const float4 v = r4[w];
+    p1 = ff_add(p1, FF{v.x, v.y});
+    p23 = ff_add(p23, FF{v.z, v.w});
+  }
+  return ff_add(ff_mul(p1, kLn2Hi, kLn2Lo), p23);
+}
+
+// The stopping rule |lnL_k - lnL_{k-1}| <= tol |lnL_k| on double-floats.
+__device__ __forceinline__ bool ff_small_change(FF cur, FF prev, float tol) {
+  const float d = (cur.hi - prev.hi) + (cur.lo - prev.lo);
+  return fabsf(d) <= tol * fabsf(cur.hi);
+}
+
 template <int M>
 __device__ __forceinline__ double lnl_total(const Sm<M> &sm) {
   const int nw = (blockDim.x + 31) >> 5;
