@@ -285,12 +285,15 @@ __device__ __forceinline__ void xpipe_drain(XPipe &pp, const Sm<M> &sm) {
 
 // Event part of the gradient of parameter p (mu_i or alpha_ij): the sum of
 // the segment slots of type i.
+// tf[i] holds the float offset of type i's first slot, (first thread + i) *
+// (M + 4), and tl[i] the number of its slots (0: no events of type i).
 template <int M>
 __device__ __forceinline__ float xseg_sum(int i, int j, const Sm<M> &sm) {
   constexpr int PP = M + 4;
-  if (sm.tstart[i + 1] <= sm.tstart[i]) return 0.f;
+  const float *ps = sm.P + sm.tf[i] + j;
+  const int cnt = sm.tl[i];
   float acc = 0.f;
-  for (int t = sm.tf[i]; t <= sm.tl[i]; ++t) acc += sm.P[(t + i) * PP + j];
+  for (int s = 0; s < cnt; ++s) acc += ps[s * PP];
   return acc;
 }
 
@@ -386,8 +389,10 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     int i0 = 0;
     while (i0 < M - 1 && sm.tstart[i0 + 1] <= p0) ++i0;
     for (int i = tid; i < M; i += NT) {
-      sm.tf[i] = sm.tstart[i] / L;
-      sm.tl[i] = sm.tstart[i + 1] > sm.tstart[i] ? (sm.tstart[i + 1] - 1) / L : -1;
+      const int first = sm.tstart[i] / L;
+      const bool has = sm.tstart[i + 1] > sm.tstart[i];
+      sm.tf[i] = (first + i) * (M + 4);
+      sm.tl[i] = has ? (sm.tstart[i + 1] - 1) / L - first + 1 : 0;
     }
     if (tid == 0) sm.ctl[3] = 0;
     __syncthreads();
@@ -407,6 +412,17 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     int streak = 0, k = 0;
     int wst = a.tol > 0.0 ? kE_MAXITER : kOK;
     float b1t = 1.f, b2t = 1.f;
+    // Part2 + Part3 of the current point: computed here for theta_0, then
+    // accumulated by the update loop while it forms theta_{k+1}
+    float Ps = 0.f, Pc = 0.f;
+    for (int p = tid; p < M + M * M; p += NT) {  // padded entries hold zeros
+      if (p < M) {
+        kahan_add(Ps, Pc, -T * sm.mu[p]);
+      } else {
+        const int qq = p - M, i = qq / M, j = qq % M;
+        kahan_add(Ps, Pc, -sm.alpha[i * AP + j] * sm.C[j]);
+      }
+    }
     for (k = 0; k < a.max_iters; ++k) {
       float Ls = 0.f, Lc = 0.f;
       if (XS) {
@@ -424,16 +440,7 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
       } else {
         xpass<M, false, NTC>(p0, p1, i0, (const float4 *)Xg, xcap, xm, sm, Ls, Lc);
       }
-      // Part2 + Part3 and the block sums (ends with a barrier)
-      float Ps = 0.f, Pc = 0.f;
-      for (int p = tid; p < M + M * M; p += NT) {  // padded entries hold zeros
-        if (p < M) {
-          kahan_add(Ps, Pc, -T * sm.mu[p]);
-        } else {
-          const int qq = p - M, i = qq / M, j = qq % M;
-          kahan_add(Ps, Pc, -sm.alpha[i * AP + j] * sm.C[j]);
-        }
-      }
+      // block sums of Part1 and Part2 + Part3 (ends with a barrier)
       float h1 = Ls, l1 = -Lc, h2 = Ps, l2 = -Pc;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -469,6 +476,8 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
       // evaluation returns the last finite point theta_{k-1}
       b1t *= a.b1;
       b2t *= a.b2;
+      Ps = 0.f;
+      Pc = 0.f;
       for (int p = tid; p < M + M * M; p += NT) {
         int i, j, pc;
         if (p < M) {
@@ -477,7 +486,8 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
           i = (p - M) / M; j = (p - M) % M; pc = Mrt + i * Mrt + j;
         }
         if (i >= Mrt || (j < M && j >= Mrt)) continue;
-        const float g = xseg_sum<M>(i, j, sm) - (j == M ? T : sm.C[j]);
+        const float cj = (j == M) ? T : sm.C[j];
+        const float g = xseg_sum<M>(i, j, sm) - cj;
         bad |= !isfinite(g);
         float &th = (j == M) ? sm.mu[i] : sm.alpha[i * AP + j];
         const float gs = g * invN;
@@ -495,7 +505,9 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
         const float fl = (j == M) ? a.mu_floor : a.alpha_floor;
         sm.prev[pc] = sm.gbuf[pc];
         sm.gbuf[pc] = th;
-        th = fmaxf(th + step, fl);
+        const float tn = fmaxf(th + step, fl);
+        th = tn;
+        kahan_add(Ps, Pc, -tn * cj);  // Part2 (-T mu_i) or Part3 (-alpha_ij C_j) of theta_{k+1}
       }
       bad = __syncthreads_or(bad);
       const int stop = bad ? 1 : sm.ctl[2];
