@@ -359,33 +359,72 @@ struct Walker {
   }
 };
 
-// Pass 1 for chunk [b0, b1) anchored at a0, ending at a1: local state -> encR/encS[c].
+// Pass 1 for chunk [b0, b1), ending at a1: the chunk's own contribution to the
+// state at a1 -> encR/encS[c].  With a scalar beta, a walk from the chunk's
+// first time a0 with one decay per timestamp.  With beta per source, each
+// event is taken directly,
+//   R_j(a1) = sum_{k in chunk, u_k = j} w_k exp(-beta_j (a1 - t_k)),
+//   S_j(a1) = sum_{k in chunk, u_k = j} w_k (a1 - t_k) exp(-beta_j (a1 - t_k)),
+// by the one thread of the chunk that owns source u_k: one exponential per
+// event instead of one per source and timestamp, and no compounding of decay
+// factors.  Every event of the chunk precedes a1 (chunk ends are moved past
+// tie groups; the last chunk ends at T_span, where d = 0).
 template <int M, int SPL, int BM, bool LEARN, typename EV>
 __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float a0, float a1,
                                             const EV &ev, const Sm<M> &sm) {
   constexpr int MS = M / SPL;
   constexpr int AP = M + 4;
   const int base = s * MS;
-  Walker<MS, BM, LEARN> wk;
-  wk.load_beta(sm.bl2, base);
-  wk.zero();
-  float tprev = a0;
-  int gs = b0;
-  for (int n = b0; n < b1; ++n) {
-    const float tn = ev.time(n);
-    if (tn > tprev) {
-      for (int k = gs; k < n; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
-      wk.decay(tn - tprev);
-      tprev = tn;
-      gs = n;
+  if constexpr (BM == 0) {
+    // one decay factor serves every source: walk the chunk from a0 (one
+    // exponential per distinct timestamp)
+    Walker<MS, BM, LEARN> wk;
+    wk.load_beta(sm.bl2, base);
+    wk.zero();
+    float tprev = a0;
+    int gs = b0;
+    for (int n = b0; n < b1; ++n) {
+      const float tn = ev.time(n);
+      if (tn > tprev) {
+        for (int k = gs; k < n; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
+        wk.decay(tn - tprev);
+        tprev = tn;
+        gs = n;
+      }
     }
+    for (int k = gs; k < b1; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
+    if (a1 > tprev) wk.decay(a1 - tprev);
+#pragma unroll
+    for (int jj = 0; jj < MS; ++jj) {
+      sm.encR[c * M + base + jj] = wk.R[jj];
+      if (LEARN) sm.encS[c * M + base + jj] = wk.S[jj];
+    }
+    return;
   }
-  for (int k = gs; k < b1; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
-  if (a1 > tprev) wk.decay(a1 - tprev);
+  float R[MS], S[LEARN ? MS : 1];
 #pragma unroll
   for (int jj = 0; jj < MS; ++jj) {
-    sm.encR[c * M + base + jj] = wk.R[jj];
-    if (LEARN) sm.encS[c * M + base + jj] = wk.S[jj];
+    R[jj] = 0.f;
+    if (LEARN) S[jj] = 0.f;
+  }
+  for (int n = b0; n < b1; ++n) {
+    const int u = ev.id(n) - base;
+    if ((unsigned)u < (unsigned)MS) {
+      const float d = a1 - ev.time(n);
+      const float we = ev.wt(n) * exp2_acc(-sm.bl2[BM == 0 ? 0 : base + u] * d);
+#pragma unroll
+      for (int jj = 0; jj < MS; ++jj) {
+        if (u == jj) {
+          R[jj] += we;
+          if (LEARN) S[jj] = fmaf(we, d, S[jj]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int jj = 0; jj < MS; ++jj) {
+    sm.encR[c * M + base + jj] = R[jj];
+    if (LEARN) sm.encS[c * M + base + jj] = S[jj];
   }
 }
 
