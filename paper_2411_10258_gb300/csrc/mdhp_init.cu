@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(128) k_features(const int64_t *offsets, const 
   int *hist = reinterpret_cast<int *>(smem);            // [M][M][kBins]
   float *lastc = reinterpret_cast<float *>(hist + M * M * kBins);  // [NT][M]
   int *cnt = reinterpret_cast<int *>(lastc + blockDim.x * M);      // [M]
+  float *invtot = reinterpret_cast<float *>(cnt + M);              // [M][M]
   const int b = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
   const int64_t o0 = offsets[b];
   const int N = (int)(offsets[b + 1] - o0);
@@ -111,11 +112,19 @@ __global__ void __launch_bounds__(128) k_features(const int64_t *offsets, const 
     for (int j = 0; j < M; ++j) {
       if (j < Mrt && lt[j] > -INFINITY) {
         const float gap = (tn - lt[j]) * scale;
-        int bin = gap > 0.f ? (int)floorf(log2f(gap)) + kBins / 2 : 0;
+        // floor(log2(gap)) of a positive float is its exponent (subnormals
+        // and the clamp below both land in bin 0)
+        int bin = gap > 0.f ? ((__float_as_int(gap) >> 23) & 0xff) - 127 + kBins / 2 : 0;
         bin = bin < 0 ? 0 : (bin >= kBins ? kBins - 1 : bin);
         atomicAdd(&hist[(i * M + j) * kBins + bin], 1);
       }
     }
+  }
+  __syncthreads();
+  for (int pair = tid; pair < M * M; pair += NT) {  // row totals of each histogram, once
+    int tot = 0;
+    for (int k = 0; k < kBins; ++k) tot += hist[pair * kBins + k];
+    invtot[pair] = tot > 0 ? 1.f / (float)tot : 0.f;
   }
   __syncthreads();
   __nv_bfloat16 *row = X + (size_t)b * K0;
@@ -127,11 +136,7 @@ __global__ void __launch_bounds__(128) k_features(const int64_t *offsets, const 
     } else if (p >= M && p < M + M * M * kBins) {
       const int q = p - M, pair = q / kBins;
       const int i = pair / M, j = pair % M;
-      if (i < Mrt && j < Mrt) {
-        int tot = 0;
-        for (int k = 0; k < kBins; ++k) tot += hist[pair * kBins + k];
-        v = tot > 0 ? (float)hist[q] / (float)tot : 0.f;
-      }
+      if (i < Mrt && j < Mrt) v = (float)hist[q] * invtot[pair];
     } else if (p == M + M * M * kBins) {
       v = logf((float)(N > 0 ? N : 1));
     } else if (p == M + M * M * kBins + 1) {
@@ -542,7 +547,7 @@ mdhp_status mdhp_init_features(const mdhp_batch *batch, const float *beta, void 
   const int M = batch->M, Mt = M <= 4 ? 4 : M <= 8 ? 8 : M <= 16 ? 16 : 32;
   const int K0 = init_k0(M);
   const int nt = 128;
-  const int smem = (Mt * Mt * kBins + nt * Mt + Mt) * 4;
+  const int smem = (Mt * Mt * kBins + nt * Mt + Mt + Mt * Mt) * 4;
   const int bstride = batch->beta_mode == MDHP_BETA_SCALAR ? 1 : M;
   cudaStream_t st = (cudaStream_t)stream;
 #define MDHP_FEAT(MV)                                                                             \
