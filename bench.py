@@ -426,6 +426,9 @@ def run_warm_cold(args):
     del feat, dtr
     plan = Plan(M, 0, B, int(bt.counts.max()))
     model.attach(plan)
+    # launch shape from the library's autotuner on this batch (untimed; tol = 0)
+    tuned = plan.autotune(db, FitOptions(optimizer=1, lr=2e-2, init=1), torch.zeros(B, M, device=dev),
+                          torch.zeros(B, M, M, device=dev), beta.clone(), tune_iters=20)
     res = {}
     for name, init in (("cold", 1), ("warm", 2)):
         opts = FitOptions(optimizer=1, max_iters=3000, lr=2e-2, tol=args.tol, init=init)
@@ -478,7 +481,8 @@ def run_warm_cold(args):
             "config": {"workload": f"{B} windows x M=32, counts log-uniform[100,10000], 10% injected "
                                    f"component, projected Adam lr 2e-2 to tol {args.tol}",
                        "init_training": f"{args.train_windows} GPU-simulated windows (generating "
-                                        f"parameters as targets), {args.train_steps} AdamW steps of 512"},
+                                        f"parameters as targets), {args.train_steps} AdamW steps of 512",
+                       "autotuned": tuned},
             "warm": res["warm"], "cold": res["cold"],
             "generating_params_start": res["generating_params_start"]}
     print(json.dumps(line), flush=True)
