@@ -176,6 +176,118 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Epilogue of a warp's 32 x 32 accumulator block at (mb, nb).
+__device__ __forceinline__ void gemm_epilogue(const GemmArgs &g, const float (&acc)[2][4][4],
+                                              int mb, int nb, int grp, int tig) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = mb + a * 16 + grp + h * 8;
+        if (m >= g.Mm) continue;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int n = nb + b * 8 + tig * 2 + cc;
+          if (n >= g.Nn) continue;
+          float v = acc[a][b][h * 2 + cc];
+          const int64_t o = (int64_t)m * g.ldc + n;
+          if (g.accumulate) {
+            g.Cf[o] += v;
+            continue;
+          }
+          if (g.bias) v += g.bias[n];
+          if (g.relu) v = fmaxf(v, 0.f);
+          if (g.Cf) g.Cf[o] = v;
+          if (g.Cb) g.Cb[o] = __float2bfloat16(v);
+        }
+      }
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 16 : 0;  // 0 source bytes: the 16 bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+// Both operands k-contiguous (A [m][k], B [n][k], rows 16-byte aligned, K a
+// multiple of 8): 64 x 64 x 64 tiles, a 3-stage cp.async pipeline (loads for
+// tile t + 2 in flight while tile t is multiplied), fragments by ldmatrix.
+constexpr int kGemmStages = 3, kGemmBK = 64, kGemmPad = 8;
+constexpr int kGemmRow = kGemmBK + kGemmPad;  // bf16 per shared row (144 bytes: conflict-free ldmatrix)
+constexpr int kGemmSmem = kGemmStages * 2 * 64 * kGemmRow * 2;
+
+__global__ void __launch_bounds__(128) k_gemm_bf16_kk(GemmArgs g) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(gsm);     // [stage][64][kGemmRow]
+  __nv_bfloat16 *Bs = As + kGemmStages * 64 * kGemmRow;            // [stage][64][kGemmRow]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int grp = lane >> 2, tig = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  const int nk = (g.Kk + kGemmBK - 1) / kGemmBK;
+  auto load_tile = [&](int t, int stage) {
+    const int k0 = t * kGemmBK;
+    __nv_bfloat16 *as = As + stage * 64 * kGemmRow, *bs = Bs + stage * 64 * kGemmRow;
+#pragma unroll
+    for (int e = tid; e < 64 * kGemmBK / 8; e += 128) {  // 4 chunks of 16 bytes per thread
+      const int r = e >> 3, kk = (e & 7) * 8;
+      const int k = k0 + kk, m = m0 + r, n = n0 + r;
+      const bool va = m < g.Mm && k < g.Kk, vb = n < g.Nn && k < g.Kk;
+      cp_async16(as + r * kGemmRow + kk, va ? g.A + (int64_t)m * g.sam + k : g.A, va);
+      cp_async16(bs + r * kGemmRow + kk, vb ? g.B + (int64_t)n * g.sbn + k : g.B, vb);
+    }
+  };
+#pragma unroll
+  for (int st = 0; st < kGemmStages - 1; ++st) {
+    if (st < nk) load_tile(st, st);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  for (int t = 0; t < nk; ++t) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kGemmStages - 2) : "memory");
+    __syncthreads();  // tile t landed for every thread; tile t - 1's buffer is free
+    if (t + kGemmStages - 1 < nk) load_tile(t + kGemmStages - 1, (t + kGemmStages - 1) % kGemmStages);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const __nv_bfloat16 *as = As + (t % kGemmStages) * 64 * kGemmRow;
+    const __nv_bfloat16 *bs = Bs + (t % kGemmStages) * 64 * kGemmRow;
+#pragma unroll
+    for (int ks = 0; ks < kGemmBK; ks += 16) {
+      uint32_t af[2][4], bq[2][4];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)  // rows wm + 16a .. +15, k ks .. ks + 15
+        ldsm_x4(af[a], as + (wm + a * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * kGemmRow + ks +
+                           (lane >> 4) * 8);
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)  // n wn + 16bb .. +15 as two n8 tiles, k ks .. ks + 15
+        ldsm_x4(bq[bb], bs + (wn + bb * 16 + (lane & 7) + (lane >> 4) * 8) * kGemmRow + ks +
+                            ((lane >> 3) & 1) * 8);
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const uint32_t bf[2] = {bq[b >> 1][(b & 1) * 2], bq[b >> 1][(b & 1) * 2 + 1]};
+          mma_bf16_16816(acc[a][b], af[a], bf);
+        }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  gemm_epilogue(g, acc, m0 + wm, n0 + wn, grp, tig);
+}
+
 __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
   constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
   __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
@@ -250,30 +362,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
     }
     __syncthreads();
   }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = m0 + wm + a * 16 + grp + h * 8;
-        if (m >= g.Mm) continue;
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int n = n0 + wn + b * 8 + tig * 2 + cc;
-          if (n >= g.Nn) continue;
-          float v = acc[a][b][h * 2 + cc];
-          const int64_t o = (int64_t)m * g.ldc + n;
-          if (g.accumulate) {
-            g.Cf[o] += v;
-            continue;
-          }
-          if (g.bias) v += g.bias[n];
-          if (g.relu) v = fmaxf(v, 0.f);
-          if (g.Cf) g.Cf[o] = v;
-          if (g.Cb) g.Cb[o] = __float2bfloat16(v);
-        }
-      }
+  gemm_epilogue(g, acc, m0 + wm, n0 + wn, grp, tig);
 }
 
 // ---------------------------------------------------------------------------
@@ -423,6 +512,15 @@ static void launch_gemm(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const 
   const int vb = (sbk == 1 && sbn % 8 == 0 && Kk % 8 == 0 && ((uintptr_t)B & 15) == 0) ? 1 : 0;
   GemmArgs g{A, B, sam, sak, sbk, sbn, Mm, Nn, Kk, bias, relu, accumulate, va, vb, Cf, Cb, ldc};
   dim3 grid((Nn + 63) / 64, (Mm + 63) / 64);
+  if (va && vb) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_gemm_bf16_kk, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+      attr = true;
+    }
+    k_gemm_bf16_kk<<<grid, 128, kGemmSmem, st>>>(g);
+    return;
+  }
   k_gemm_bf16<<<grid, 128, 0, st>>>(g);
 }
 
