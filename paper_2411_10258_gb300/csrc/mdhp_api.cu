@@ -184,6 +184,10 @@ struct mdhp_plan {
   mdhp_init_model *model = nullptr;  // learned initializer (not owned)
   std::string cache;                 // autotune cache file ("" = none)
   int launches = 0;                  // kernel launches of the last mdhp_fit_batch
+  // recursion fit: theta_{k-1} per resident CTA in device memory (frees
+  // shared memory for a second CTA per SM at M = 64)
+  float *pbuf = nullptr;
+  int pslots = 0, pstride = 0;
 };
 
 // --- autotuner: cache of tuned launch shapes ---------------------------------
@@ -265,7 +269,7 @@ int stage_fit(const mdhp_plan *p, int nt, int spl, bool weights, bool learn, boo
   int lo = 0, hi = 1 << 20;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
-    if (make_carve(p->Mt, nt, spl, mid, weights, learn, adam, true, use_priv(p->Mt)).total <=
+    if (make_carve(p->Mt, nt, spl, mid, weights, learn, adam, true, use_priv(p->Mt), false).total <=
         max_dyn_smem())
       lo = mid;
     else
@@ -554,6 +558,9 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
   ok &= cudaMalloc(&p->idx, sizeof(int) * max_windows) == cudaSuccess;
   ok &= cudaMalloc(&p->order, sizeof(int) * max_windows) == cudaSuccess;
   ok &= cudaMalloc(&p->ctl, sizeof(int) * 16) == cudaSuccess;
+  p->pstride = (p->Mt + p->Mt * p->Mt + p->Mt + 63) / 64 * 64;
+  p->pslots = num_sms() * 16;
+  ok &= cudaMalloc(&p->pbuf, sizeof(float) * (size_t)p->pslots * p->pstride) == cudaSuccess;
   if (ok) {
     cub::DeviceRadixSort::SortPairsDescending(nullptr, p->sort_tmp_bytes, p->keys, p->keys_sorted,
                                               p->idx, p->order, max_windows);
@@ -632,6 +639,7 @@ void mdhp_plan_destroy(mdhp_plan *p) {
   cudaFree(p->idx);
   cudaFree(p->order);
   cudaFree(p->ctl);
+  cudaFree(p->pbuf);
   cudaFree(p->sort_tmp);
   cudaFree(p->xbuf);
   if (p->side) cudaStreamDestroy(p->side);
@@ -887,12 +895,15 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     al.queue = p->ctl + 0;
     al.range = p->ctl + 2;
     al.ev_cap = 0;
+    al.pbuf = p->pbuf;
+    al.pstride = p->pstride;
     al.carve = make_carve(p->Mt, sh.nt, sh.spl, 0, batch->weights != nullptr, learn,
-                          o->optimizer == 1, true, use_priv(p->Mt));
+                          o->optimizer == 1, true, use_priv(p->Mt), false);
     if ((s = prepare_kernel((const void *)fl, al.carve.total)) != MDHP_OK) return s;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fl, sh.nt, al.carve.total);
-    const int grid = num_sms() * (occ > 0 ? occ : 1);
+    int grid = num_sms() * (occ > 0 ? occ : 1);
+    if (grid > p->pslots) grid = p->pslots;
     fl<<<grid, sh.nt, al.carve.total, st>>>(al);
     ++p->launches;
     if ((s = cuda_check("k_fit (streamed)")) != MDHP_OK) return s;
@@ -904,8 +915,10 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     as.queue = p->ctl + 1;
     as.range = p->ctl + 4;
     as.ev_cap = ev_cap;
+    as.pbuf = p->pbuf;
+    as.pstride = p->pstride;
     as.carve = make_carve(p->Mt, sh.nt, sh.spl, ev_cap, batch->weights != nullptr, learn,
-                          o->optimizer == 1, true, use_priv(p->Mt));
+                          o->optimizer == 1, true, use_priv(p->Mt), false);
     if (as.carve.total > max_dyn_smem())
       return fail(MDHP_E_ARG, "shared memory %d > %d (lower the cutoff)", as.carve.total, max_dyn_smem());
     if ((s = prepare_kernel((const void *)fs, as.carve.total)) != MDHP_OK) return s;
@@ -913,6 +926,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fs, sh.nt, as.carve.total);
     int grid = num_sms() * (occ > 0 ? occ : 1);
     if (grid > B) grid = B;
+    if (grid > p->pslots) grid = p->pslots;
     fs<<<grid, sh.nt, as.carve.total, st>>>(as);
     ++p->launches;
     if ((s = cuda_check("k_fit (staged)")) != MDHP_OK) return s;

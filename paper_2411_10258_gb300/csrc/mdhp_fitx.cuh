@@ -84,7 +84,7 @@ __device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, in
     int un;
     ev.get(n, tn, un);
     if (tn > tprev) {
-      for (int k = gs; k < n; ++k) wk.add(sm.oh + ev.id(k) * AP, ev.wt(k));
+      for (int k = gs; k < n; ++k) wk.add(ev.id(k), ev.wt(k));
       wk.decay(tn - tprev);
       tprev = tn;
       gs = n;

@@ -40,6 +40,8 @@ struct FitArgs {
   float lr, mu_floor, alpha_floor, beta_floor, b1, b2, eps;
   double tol;
   float4 *xbuf;  // decoupled fit: per-CTA feature scratch (global), or nullptr
+  float *pbuf;   // recursion fit: per-CTA slot (pstride floats) for theta_{k-1}, or nullptr
+  int pstride;   //   (nullptr: theta_{k-1} is kept in shared memory)
   int pipe_steps, pipe_stages;  // streamed features: bulk-copy ring (0 stages: register prefetch)
   // decoupled fit, two launches sharing one length-sorted range: qdir 1 takes
   // windows from the front (longest first), qdir 2 from the back; dq =
@@ -71,7 +73,6 @@ __device__ void load_params(int b, int Mrt, const float *mu, const float *alpha,
   for (int p = threadIdx.x; p < M * AP; p += blockDim.x) {
     const int i = p / AP, j = p % AP;
     sm.alpha[p] = (i < Mrt && j < Mrt) ? alpha[(int64_t)b * Mrt * Mrt + i * Mrt + j] : 0.f;
-    sm.oh[p] = (i == j) ? 1.f : 0.f;
   }
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
     sm.mu[j] = j < Mrt ? mu[(int64_t)b * Mrt + j] : 0.f;
@@ -165,6 +166,9 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
   const int np = Mrt + Mrt * Mrt + nb;
   const int nupd = a.fit_beta ? np : Mrt + Mrt * Mrt;
   const int tid = threadIdx.x;
+  // theta_{k-1} (restored after a non-finite evaluation): the CTA's device
+  // slot when the launch provides one, else shared memory
+  float *prevp = a.pbuf ? a.pbuf + (size_t)blockIdx.x * a.pstride : sm.prev;
   constexpr bool FIXED = std::is_same<EV, EvS>::value && !LEARN && BM == 0;
   setup_chunks(a.NC, N, T, ev, sm.bnd, sm.anc);
   if (!LEARN) prepare_states<M, SPL, BM, false>(a.NC, ev, Mrt, sm);
@@ -205,7 +209,7 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
     bad = __syncthreads_or(bad);
     if (bad) {
       if (k > 0) {
-        for (int p = tid; p < nupd; p += blockDim.x) param_ref<M>(p, Mrt, sm) = sm.prev[p];
+        for (int p = tid; p < nupd; p += blockDim.x) param_ref<M>(p, Mrt, sm) = prevp[p];
       }
       wst = kE_NONFINITE;
       __syncthreads();
@@ -229,7 +233,7 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
         step = a.lr * g;
       }
       const float fl = p < Mrt ? a.mu_floor : (p < Mrt + Mrt * Mrt ? a.alpha_floor : a.beta_floor);
-      sm.prev[p] = th;
+      prevp[p] = th;
       th = fmaxf(th + step, fl);
     }
     __syncthreads();  // the event sums were read; parameters updated

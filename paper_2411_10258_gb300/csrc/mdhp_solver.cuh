@@ -172,7 +172,8 @@ __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a *
 __host__ __device__ inline int pitch4(int M) { return M + 4; }  // 16-byte rows, staggered banks
 
 __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, bool weights,
-                                            bool learn, bool adam, bool fit, bool priv) {
+                                            bool learn, bool adam, bool fit, bool priv,
+                                            bool prev_smem = true) {
   const int NC = NT / SPL;
   Carve c = {};
   int o = 0;
@@ -182,7 +183,6 @@ __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, 
   c.red = take(32 * 8);
   c.ctl = take(16 * 4);
   c.alpha = take(M * AP * 4);
-  c.oh = take(M * AP * 4);
   c.ga = priv ? 0 : take(M * (M + 1) * 4);
   c.mu = take(M * 4);
   c.gm = take(M * 4);
@@ -199,7 +199,7 @@ __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, 
   c.bnd = take((NC + 1) * 4);
   c.encR = take(NC * M * 4);
   c.encS = learn ? take(NC * M * 4) : c.encR;
-  c.prev = fit ? take(npm * 4) : 0;
+  c.prev = (fit && prev_smem) ? take(npm * 4) : 0;  // else in the launch's per-CTA device slot
   c.gbuf = fit ? take(npm * 4) : 0;
   c.am = (fit && adam) ? take(npm * 4) : 0;
   c.av = (fit && adam) ? take(npm * 4) : 0;
@@ -227,7 +227,6 @@ __host__ __device__ inline Carve make_carve_x(int M, int NT, int xcap, bool adam
   c.red = take(32 * 8);
   c.ctl = take(16 * 4);
   c.alpha = take(M * AP * 4);
-  c.oh = take(M * AP * 4);
   c.mu = take(M * 4);
   c.gm = take(M * 4);
   c.beta = take(M * 4);
@@ -345,17 +344,11 @@ struct Walker {
       }
     }
   }
-  // R += w * e_u restricted to my sources: one row of the identity table
-  __device__ __forceinline__ void add(const float *oh_row, float w) {
-    const float4 *o4 = reinterpret_cast<const float4 *>(oh_row);
+  // R += w * e_u restricted to my sources; u_rel = u - (first source of this
+  // thread), outside [0, MS) for another thread's source
+  __device__ __forceinline__ void add(int u_rel, float w) {
 #pragma unroll
-    for (int q = 0; q < MS / 4; ++q) {
-      const float4 o = o4[q];
-      R[4 * q + 0] = fmaf(o.x, w, R[4 * q + 0]);
-      R[4 * q + 1] = fmaf(o.y, w, R[4 * q + 1]);
-      R[4 * q + 2] = fmaf(o.z, w, R[4 * q + 2]);
-      R[4 * q + 3] = fmaf(o.w, w, R[4 * q + 3]);
-    }
+    for (int jj = 0; jj < MS; ++jj) R[jj] += (jj == u_rel) ? w : 0.f;
   }
 };
 
@@ -386,13 +379,13 @@ __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float 
     for (int n = b0; n < b1; ++n) {
       const float tn = ev.time(n);
       if (tn > tprev) {
-        for (int k = gs; k < n; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
+        for (int k = gs; k < n; ++k) wk.add(ev.id(k) - base, ev.wt(k));
         wk.decay(tn - tprev);
         tprev = tn;
         gs = n;
       }
     }
-    for (int k = gs; k < b1; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
+    for (int k = gs; k < b1; ++k) wk.add(ev.id(k) - base, ev.wt(k));
     if (a1 > tprev) wk.decay(a1 - tprev);
 #pragma unroll
     for (int jj = 0; jj < MS; ++jj) {
@@ -482,9 +475,9 @@ __device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float 
     ev.get(n, tn, un);
     if (tn > tprev) {
       if (n - gs == 1) {
-        wk.add(sm.oh + pu * AP + base, pw);
+        wk.add(pu - base, pw);
       } else {
-        for (int k = gs; k < n; ++k) wk.add(sm.oh + ev.id(k) * AP + base, ev.wt(k));
+        for (int k = gs; k < n; ++k) wk.add(ev.id(k) - base, ev.wt(k));
       }
       wk.decay(tn - tprev);
       tprev = tn;
@@ -603,13 +596,6 @@ __device__ void setup_chunks(int NC, int N, float T, const EV &ev, int *bnd, flo
   __syncthreads();
 }
 
-// Identity table used for the increments (rows padded to the alpha pitch).
-template <int M>
-__device__ void fill_onehot(Sm<M> &sm) {
-  constexpr int AP = M + 4;
-  for (int p = threadIdx.x; p < M * AP; p += blockDim.x) sm.oh[p] = (p / AP == p % AP) ? 1.f : 0.f;
-}
-
 // Pass 1 + scan + compensator constants.  Leaves C, dC, endR, endS in smem.
 template <int M, int SPL, int BM, bool LEARN, typename EV>
 __device__ void prepare_states(int NC, const EV &ev, int Mrt, Sm<M> &sm) {
@@ -715,9 +701,9 @@ __device__ __forceinline__ void pass2_fixed(int c, int s, int b0, int b1, const 
     const int un = cd & 0x7fff;
     if (cd & 0x8000) {
       if (n - gs == 1) {
-        wk.add(sm.oh + pu * AP + base, pw);
+        wk.add(pu - base, pw);
       } else {
-        for (int k = gs; k < n; ++k) wk.add(sm.oh + ((int)U[k] & 0x7fff) * AP + base, w ? w[k] : 1.f);
+        for (int k = gs; k < n; ++k) wk.add(((int)U[k] & 0x7fff) - base, w ? w[k] : 1.f);
       }
 #pragma unroll
       for (int jj = 0; jj < MS; ++jj) wk.R[jj] *= an;
