@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 5],
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 5, 6],
                     help="2: fixed-iteration fits (default line); 5: warm vs cold fits to tolerance")
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--no-autotune", action="store_true")
@@ -149,10 +149,15 @@ def feature_bytes_per_event_iter(M: int) -> int:
     return 4 * M
 
 
+WORKLOAD6 = ("4096 windows x M=16, counts log-uniform[200,5000], beta_ij matrix log-uniform[0.5,2] "
+             "fixed, 200 PGD iterations (lr 1e-2), cold start")
+
+
 def make_inputs(args, rank):
     from paper_2411_10258_gb300.workload import workload
 
-    bt = workload.make_workload(2, B=args.windows, seed=2024 + rank, beta=args.beta)
+    name = 6 if args.workload == 6 else 2
+    bt = workload.make_workload(name, B=args.windows, seed=2024 + rank, beta=args.beta)
     return bt
 
 
@@ -247,7 +252,7 @@ def run_ours(args):
     B, M = bt.B, bt.M
     max_ev = int(bt.counts.max())
     db = DeviceBatch.from_host(bt, dev)
-    plan = Plan(M, 0, B, max_ev)
+    plan = Plan(M, bt.beta_mode, B, max_ev)
     opts = FitOptions(max_iters=args.iters, lr=1e-2, init=1)
     beta = torch.from_numpy(bt.beta.astype(np.float32)).to(dev)
     mu = torch.zeros(B, M, device=dev)
@@ -305,7 +310,8 @@ def run_ours(args):
 
     peaks, src = measured_peaks()
     traffic = args.traffic
-    if traffic is None and B == 4096 and M == 16 and args.iters == 200 and args.beta == 1.0:
+    if traffic is None and B == 4096 and M == 16 and args.iters == 200 and args.beta == 1.0 \
+            and args.workload == 2:
         traffic = FIT_DRAM_BYTES_4096xM16
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = fp32_peak_tflops(sm_count, float(peaks.get("sm_max_mhz", 2070.0)))
@@ -315,7 +321,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "windows_per_gpu": B, "M": M,
+            "config": {"workload": WORKLOAD6 if args.workload == 6 else WORKLOAD,
+                       "windows_per_gpu": B, "M": M,
                        "events_per_gpu": int(bt.n_events), "iterations": args.iters,
                        "parallelism": f"windows sharded over {world} GPU(s), no collective",
                        "l2": "flushed (256 MB write) before every timed step",
@@ -369,7 +376,7 @@ def e2e_run(args, bt, plan, opts, dev):
     def one():
         for k in dev_bufs:
             dev_bufs[k].copy_(host[k], non_blocking=True)
-        db = DeviceBatch(M, 0, dev_bufs["offsets"], dev_bufs["t"], dev_bufs["id"], dev_bufs["T"],
+        db = DeviceBatch(M, bt.beta_mode, dev_bufs["offsets"], dev_bufs["t"], dev_bufs["id"], dev_bufs["T"],
                          None, int(bt.counts.max()))
         out = plan.fit(db, opts, mu, alpha, dev_bufs["beta"])
         res_h["loglik"].copy_(out["loglik"], non_blocking=True)
@@ -564,7 +571,7 @@ def main():
         run_warm_cold(args)
     elif args.workload == 3:
         run_long_learned(args)
-    else:
+    else:  # 2, or 6 (the same with the full decay matrix)
         run_ours(args)
 
 

@@ -29,8 +29,10 @@
  *     the call itself then still returns MDHP_OK.  MDHP_E_CUDA means a launch
  *     failed; mdhp_last_error() gives the text.
  *   - Gradients are of lnL itself (ascent direction), not of -lnL.
- *   - Matrix-shaped beta (MDHP_BETA_MATRIX) is not supported on the GPU path:
- *     such calls return MDHP_E_UNSUPPORTED.
+ *   - Matrix-shaped beta (MDHP_BETA_MATRIX, the paper's general form) is
+ *     supported by mdhp_fit_batch with a fixed beta (fit_beta = 0) for M <= 32
+ *     on a plan with a stated max_events_per_window (the decoupled kernels);
+ *     every other call with matrix beta returns MDHP_E_UNSUPPORTED.
  *   - M (number of event types / message IDs) is limited to 1..64.
  */
 #ifndef MDHP_H_
@@ -61,7 +63,7 @@ typedef enum {
 typedef enum {
   MDHP_BETA_SCALAR = 0,     /* beta[B]: one decay per window */
   MDHP_BETA_PER_SOURCE = 1, /* beta[B][M]: beta_ij = beta_j (decay of source j's excitation) */
-  MDHP_BETA_MATRIX = 2      /* beta[B][M][M]: the paper's general (D, D) form (oracle only) */
+  MDHP_BETA_MATRIX = 2      /* beta[B][M][M]: the paper's general (D, D) form (fixed-beta fits) */
 } mdhp_beta_mode;
 
 /*

@@ -16,6 +16,16 @@ FitFn get_fit_m4(int SPL, int BM, bool learn, bool stage) {
 WgFn get_wg_m4(int BM) { return BM == 0 ? k_weight_grad<4, 0> : k_weight_grad<4, 1>; }
 
 FitFn get_fitx_m4(int BM, int xm, int nt) {
+  if (BM == 2) {  // matrix beta (fixed): global or shared-memory features
+    if (xm == XM_SHARED) return k_fit_x<4, 2, XM_SHARED, 0>;
+    if (xm != XM_GLOBAL) return nullptr;
+    switch (nt) {
+      case 64: return k_fit_x<4, 2, XM_GLOBAL, 64>;
+      case 128: return k_fit_x<4, 2, XM_GLOBAL, 128>;
+      case 256: return k_fit_x<4, 2, XM_GLOBAL, 256>;
+    }
+    return nullptr;
+  }
   if (BM != 0 && BM != 1) return nullptr;
   if (xm == XM_SHARED) return BM == 0 ? k_fit_x<4, 0, XM_SHARED, 0> : k_fit_x<4, 1, XM_SHARED, 0>;
   if (xm == XM_RING) return BM == 0 ? k_fit_x<4, 0, XM_RING, 0> : k_fit_x<4, 1, XM_RING, 0>;

@@ -135,13 +135,14 @@ static mdhp_status prepare_kernel(const void *fn, int smem) {
   return MDHP_OK;
 }
 
-static mdhp_status check_batch(const mdhp_batch *b) {
+static mdhp_status check_batch(const mdhp_batch *b, bool matrix_ok = false) {
   if (!b) return fail(MDHP_E_ARG, "batch is NULL");
   if (b->B < 0) return fail(MDHP_E_ARG, "B < 0");
   if (b->M < 1 || b->M > 64) return fail(MDHP_E_ARG, "M = %d outside 1..64", b->M);
-  if (b->beta_mode == MDHP_BETA_MATRIX)
-    return fail(MDHP_E_UNSUPPORTED, "matrix-shaped beta is not implemented on the GPU path");
-  if (b->beta_mode != MDHP_BETA_SCALAR && b->beta_mode != MDHP_BETA_PER_SOURCE)
+  if (b->beta_mode == MDHP_BETA_MATRIX && !matrix_ok)
+    return fail(MDHP_E_UNSUPPORTED, "matrix-shaped beta: only mdhp_fit_batch with a fixed beta");
+  if (b->beta_mode != MDHP_BETA_SCALAR && b->beta_mode != MDHP_BETA_PER_SOURCE &&
+      b->beta_mode != MDHP_BETA_MATRIX)
     return fail(MDHP_E_ARG, "beta_mode %d", b->beta_mode);
   if (b->n_events < 0) return fail(MDHP_E_ARG, "n_events < 0");
   if (b->n_events > 0 && (!b->t || !b->id)) return fail(MDHP_E_ARG, "t/id NULL");
@@ -258,7 +259,7 @@ int field_int(const std::string &entry, const char *name, int dflt) {
 // largest events-per-window class of the decoupled kernels that fits the
 // shared memory of one CTA of nt threads (0 if none)
 int xres_fit(const mdhp_plan *p, int nt, bool adam) {
-  const int fixed = make_carve_x(p->Mt, nt, 0, adam).total;
+  const int fixed = make_carve_x(p->Mt, nt, 0, adam, 0, 0, p->beta_mode == 2).total;
   int fit = ((max_dyn_smem() - 1024 - fixed) / (p->Mt * 4)) / 32 * 32;
   if (fit > p->xcap) fit = p->xcap / 32 * 32;
   return fit >= 64 ? fit : 0;
@@ -375,8 +376,8 @@ mdhp_status launch_dual(mdhp_plan *p, const FitArgs &ax, bool adam, cudaStream_t
   aL.pipe_stages = aS.pipe_stages = 0;
   aL.qdir = 1;
   aS.qdir = 2;
-  aL.carve = make_carve_x(p->Mt, ntL, 0, adam);
-  aS.carve = make_carve_x(p->Mt, ntS, 0, adam);
+  aL.carve = make_carve_x(p->Mt, ntL, 0, adam, 0, 0, p->beta_mode == 2);
+  aS.carve = make_carve_x(p->Mt, ntS, 0, adam, 0, 0, p->beta_mode == 2);
   mdhp_status s;
   if ((s = prepare_kernel((const void *)fL, aL.carve.total)) != MDHP_OK) return s;
   if ((s = prepare_kernel((const void *)fS, aS.carve.total)) != MDHP_OK) return s;
@@ -539,9 +540,11 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
   if (!out) return fail(MDHP_E_ARG, "plan out-pointer NULL");
   *out = nullptr;
   if (M < 1 || M > 64) return fail(MDHP_E_ARG, "M = %d outside 1..64", M);
-  if (beta_mode == MDHP_BETA_MATRIX)
-    return fail(MDHP_E_UNSUPPORTED, "matrix-shaped beta is not implemented on the GPU path");
-  if (beta_mode != 0 && beta_mode != 1) return fail(MDHP_E_ARG, "beta_mode %d", beta_mode);
+  if (beta_mode != 0 && beta_mode != 1 && beta_mode != 2)
+    return fail(MDHP_E_ARG, "beta_mode %d", beta_mode);
+  if (beta_mode == MDHP_BETA_MATRIX && (M > 32 || max_events_per_window <= 0))
+    return fail(MDHP_E_UNSUPPORTED,
+                "matrix-shaped beta needs M <= 32 and a stated max_events_per_window (decoupled kernels)");
   if (max_windows < 1) return fail(MDHP_E_ARG, "max_windows < 1");
   if (max_events_per_window < 0) return fail(MDHP_E_ARG, "max_events_per_window < 0");
   mdhp_plan *p = new mdhp_plan();
@@ -571,7 +574,7 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
     int slots = 0;
     for (int nt = 64; nt <= 256; nt *= 2) {
       FitFn fx = get_fitx(p->Mt, beta_mode, XM_GLOBAL, nt);
-      const Carve cx = make_carve_x(p->Mt, nt, 0, true);
+      const Carve cx = make_carve_x(p->Mt, nt, 0, true, 0, 0, beta_mode == 2);
       int occ = 0;
       if (fx && prepare_kernel((const void *)fx, cx.total) == MDHP_OK &&
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fx, nt, cx.total) == cudaSuccess &&
@@ -593,13 +596,13 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
     }
     // shared-memory class: two CTAs per SM for M <= 16, one for M = 32
     FitFn fr = get_fitx(p->Mt, beta_mode, XM_SHARED, p->xnt);
-    const int fixed = make_carve_x(p->Mt, p->xnt, 0, true).total;
+    const int fixed = make_carve_x(p->Mt, p->xnt, 0, true, 0, 0, beta_mode == 2).total;
     const int target = (p->Mt <= 16 ? max_dyn_smem() / 2 : max_dyn_smem()) - 1024;
     int cap = (target - fixed) / (p->Mt * 4);
     cap = cap / 32 * 32;
     if (p->xbuf && fr && cap >= 64) {
       if (cap > p->xcap) cap = p->xcap;
-      const Carve cr = make_carve_x(p->Mt, p->xnt, cap, true);
+      const Carve cr = make_carve_x(p->Mt, p->xnt, cap, true, 0, 0, beta_mode == 2);
       int occr = 0;
       if (prepare_kernel((const void *)fr, cr.total) == MDHP_OK &&
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occr, fr, p->xnt, cr.total) == cudaSuccess &&
@@ -734,7 +737,8 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *p, int32_t nt, int32_t spl, int32_t c
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
   if (nt < 32 || nt > 256 || nt % 32 != 0) return fail(MDHP_E_ARG, "threads per window %d (32..256, multiple of 32)", nt);
   if (nt < p->Mt) return fail(MDHP_E_ARG, "threads per window must be >= %d", p->Mt);
-  if (!get_fit(p->Mt, spl, p->beta_mode, false, true))
+  // (matrix beta runs only the decoupled kernels, which have no chunk split)
+  if (p->beta_mode != MDHP_BETA_MATRIX && !get_fit(p->Mt, spl, p->beta_mode, false, true))
     return fail(MDHP_E_UNSUPPORTED, "threads per chunk %d not built for M<=%d", spl, p->Mt);
   if (cutoff < 0) return fail(MDHP_E_ARG, "cutoff < 0");
   p->shape = Shape{nt, spl, cutoff};
@@ -748,13 +752,21 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
                            float *mu, float *alpha, float *beta, double *loglik, int32_t *iters,
                            int32_t *win_status, void *stream) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
-  mdhp_status s = check_batch(batch);
+  mdhp_status s = check_batch(batch, true);
   if (s != MDHP_OK) return s;
   if (!o) return fail(MDHP_E_ARG, "opts NULL");
   if (batch->M != p->M || batch->beta_mode != p->beta_mode)
     return fail(MDHP_E_ARG, "batch (M=%d, beta_mode=%d) does not match plan (M=%d, %d)", batch->M,
                 batch->beta_mode, p->M, p->beta_mode);
   if (batch->B > p->max_windows) return fail(MDHP_E_ARG, "B=%d > plan max_windows=%d", batch->B, p->max_windows);
+  if (p->beta_mode == MDHP_BETA_MATRIX) {  // decoupled kernels only
+    const int64_t bnd = batch->max_events > 0 ? batch->max_events : p->max_events;
+    if (o->fit_beta) return fail(MDHP_E_UNSUPPORTED, "matrix-shaped beta cannot be learned on the GPU");
+    if (o->init == 2) return fail(MDHP_E_UNSUPPORTED, "no learned initializer for matrix-shaped beta");
+    if (!p->use_x || !p->xbuf || bnd <= 0 || bnd > p->xcap)
+      return fail(MDHP_E_UNSUPPORTED, "matrix-shaped beta needs the decoupled kernels (path auto, "
+                                      "windows within the plan's max_events_per_window)");
+  }
   if (o->max_iters < 1) return fail(MDHP_E_ARG, "max_iters < 1");
   if (o->optimizer != 0 && o->optimizer != 1) return fail(MDHP_E_ARG, "optimizer %d", o->optimizer);
   if (o->init < 0 || o->init > 2) return fail(MDHP_E_ARG, "init %d", o->init);
@@ -797,7 +809,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   // decoupled path: windows longer than the shared-memory class form the first range
   int xcut = -1;
   if (p->xres > 0) {
-    const int fixed = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1).total;
+    const int fixed = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1, 0, 0, p->beta_mode == 2).total;
     const int fit = ((max_dyn_smem() - 1024 - fixed) / (p->Mt * 4)) / 32 * 32;
     xcut = p->xres < fit ? p->xres : fit;
     if (xcut < 64) xcut = -1;
@@ -818,7 +830,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
 
   int xres = p->xres;
   if (xpath && xres > 0) {  // the largest class that fits this block size
-    const int fixed = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1).total;
+    const int fixed = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1, 0, 0, p->beta_mode == 2).total;
     const int fit = ((max_dyn_smem() - 1024 - fixed) / (p->Mt * 4)) / 32 * 32;
     if (xres > fit) xres = fit;
     if (xres < 64) xres = 0;
@@ -842,10 +854,12 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
       al.ev_cap = p->xcap;
       al.pipe_steps = p->pipe_steps;
       al.pipe_stages = p->pipe_stages;
-      al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1, p->pipe_steps, p->pipe_stages);
+      if (p->beta_mode == 2) al.pipe_stages = 0;  // the ring is not built for matrix beta
+      al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1, p->pipe_steps, al.pipe_stages,
+                              p->beta_mode == 2);
       if (al.pipe_stages > 0 && al.carve.total > max_dyn_smem()) {  // ring too large for this block
         al.pipe_stages = 0;
-        al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1);
+        al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1, 0, 0, p->beta_mode == 2);
       }
       FitFn fx = get_fitx(p->Mt, p->beta_mode, al.pipe_stages > 0 ? XM_RING : XM_GLOBAL, p->xnt);
       if ((s = prepare_kernel((const void *)fx, al.carve.total)) != MDHP_OK) return s;
@@ -870,7 +884,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
       ar.queue = p->ctl + 1;
       ar.range = p->ctl + 4;
       ar.ev_cap = xres;
-      ar.carve = make_carve_x(p->Mt, p->xnt, xres, o->optimizer == 1);
+      ar.carve = make_carve_x(p->Mt, p->xnt, xres, o->optimizer == 1, 0, 0, p->beta_mode == 2);
       if ((s = prepare_kernel((const void *)fr, ar.carve.total)) != MDHP_OK) return s;
       int occr = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occr, fr, p->xnt, ar.carve.total);
@@ -943,7 +957,7 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
                                int32_t *win_status, int32_t tune_iters, int32_t *chosen,
                                float *best_ms, void *stream) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
-  mdhp_status s = check_batch(batch);
+  mdhp_status s = check_batch(batch, true);
   if (s != MDHP_OK) return s;
   if (!o) return fail(MDHP_E_ARG, "opts NULL");
   if (!mu || !alpha || !beta || !loglik || !iters || !win_status)
@@ -990,7 +1004,9 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
     if (path == 0) {
       const int fit = xres_fit(p, nt, adam);
       for (const auto &pd : kPipes) {
-        if (pd[1] > 0 && make_carve_x(p->Mt, nt, 0, adam, pd[0], pd[1]).total > max_dyn_smem()) continue;
+        if (pd[1] > 0 && (p->beta_mode == 2 ||
+                          make_carve_x(p->Mt, nt, 0, adam, pd[0], pd[1]).total > max_dyn_smem()))
+          continue;
         cands.push_back({nt, 0, 0, pd[0], pd[1], 0, 256, 1});
         if (fit >= 64) cands.push_back({nt, 0, fit, pd[0], pd[1], 0, 256, 1});
       }

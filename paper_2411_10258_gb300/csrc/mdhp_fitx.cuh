@@ -99,6 +99,132 @@ __device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, in
   __syncthreads();
 }
 
+// Features for a fixed MATRIX beta (beta_ij per pair).  The row of an event n
+// of type i is R_i.(t_n), R_ij(t) = sum_{k: t_k < t, u_k = j} w_k exp(-beta_ij
+// (t - t_k)), so the iteration pass is the same as for the other beta shapes.
+// One thread per (target row i, chunk c), NCm = NT / M chunks.  A row is kept
+// lazily as S_j at an anchor time ta, R_ij(t) = 2^(-b_ij (t - ta)) S_j with
+// b_ij = beta_ij log2(e): an event k of type j adds w_k 2^(+b_ij (t_k - ta))
+// to S_j (one exponential per event and row); at an event of type i the row is
+// materialised (M exponentials), written as that event's features and
+// re-anchored there; if the positive exponent would pass 64 the row is
+// re-anchored early.  Pass 1 gives each (i, c) its chunk's end state from
+// zero, a per-pair scan over chunks the entering states and R_ij(T), hence
+// C_ij = (W_j - R_ij(T)) / beta_ij; pass 2 writes the features at their
+// type-sorted positions.  About 3M exponentials per event over all rows.
+// S lives in shared memory ([j][thread], in P after the per-type counters).
+template <int M, bool XS, typename EV, typename XP>
+__device__ void build_features_matrix(int N, float T, const EV &ev, int Mrt, Sm<M> &sm, XP X,
+                                      int xcap, XMap m) {
+  constexpr int NQ = M / 4;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int NCm = NT / M;
+  const int i = tid % M, c = tid / M;
+  const bool act = c < NCm && i < Mrt;
+  setup_chunks(NCm, N, T, ev, sm.bnd, sm.anc);  // ends with a barrier
+  int *ctr = reinterpret_cast<int *>(sm.P);      // [type][chunk] counts, then positions
+  float *S = sm.P + NT;                          // [j][thread]
+  const float *bl = sm.bl2 + i * M;
+  const int b0 = act ? sm.bnd[c] : 0, b1 = act ? sm.bnd[c + 1] : 0;
+  const float a0 = act ? sm.anc[c] : 0.f, a1 = act ? sm.anc[c + 1] : 0.f;
+  float bmax = 0.f;
+  for (int j = 0; j < Mrt; ++j) bmax = fmaxf(bmax, bl[j]);
+  if (act) {
+    int cnt = 0;
+    for (int n = b0; n < b1; ++n) cnt += ev.id(n) == i ? 1 : 0;
+    ctr[i * NCm + c] = cnt;
+  }
+  if (tid == 0) {
+    int acc = 0;
+    for (int k = 0; k < M; ++k) {
+      sm.tstart[k] = acc;
+      acc += (k < Mrt) ? sm.cnt[k] : 0;
+    }
+    sm.tstart[M] = acc;
+  }
+  __syncthreads();
+  if (tid < Mrt) {  // exclusive scan over chunks, per type, from the type's start
+    int run = sm.tstart[tid];
+    for (int cc = 0; cc < NCm; ++cc) {
+      const int v = ctr[tid * NCm + cc];
+      ctr[tid * NCm + cc] = run;
+      run += v;
+    }
+  }
+  // the lazy row walk; WRITE: materialise and write at the events of type i
+  auto walk = [&](bool write) {
+    float ta = a0, tprev = a0;
+    int gs = b0;
+    auto add = [&](int k) {
+      const float tk = ev.time(k);
+      float d = tk - ta;
+      if (bmax * d > 64.f) {  // re-anchor at tk before the exponent grows too large
+        for (int j = 0; j < M; ++j) S[j * NT + tid] *= exp2_acc(-bl[j] * d);
+        ta = tk;
+        d = 0.f;
+      }
+      const int u = ev.id(k);
+      S[u * NT + tid] += ev.wt(k) * exp2_acc(bl[u] * d);
+    };
+    for (int n = b0; n < b1; ++n) {
+      const float tn = ev.time(n);
+      if (tn > tprev) {  // the previous tie group becomes history
+        for (int k = gs; k < n; ++k) add(k);
+        tprev = tn;
+        gs = n;
+      }
+      if (write && ev.id(n) == i) {
+        const float d = tn - ta;
+        float x[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          x[j] = S[j * NT + tid] * exp2_acc(-bl[j] * d);
+          S[j * NT + tid] = x[j];
+        }
+        ta = tn;
+        const int pos = ctr[i * NCm + c];
+        ctr[i * NCm + c] = pos + 1;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          X[xidx<XS>(q, pos, xcap, NQ, m)] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+      }
+    }
+    for (int k = gs; k < b1; ++k) add(k);
+    return ta;
+  };
+  // pass 1: each chunk's own contribution to the state at its end
+  if (act) {
+    for (int j = 0; j < M; ++j) S[j * NT + tid] = 0.f;
+    const float ta = walk(false);
+    for (int j = 0; j < M; ++j) sm.encR[(c * M + i) * M + j] = S[j * NT + tid] * exp2_acc(-bl[j] * (a1 - ta));
+  }
+  __syncthreads();
+  // per-pair scan: entering states, R_ij(T), C_ij
+  for (int p = tid; p < M * M; p += NT) {
+    const int ii = p / M, jj = p % M;
+    if (ii < Mrt && jj < Mrt) {
+      float R = 0.f;
+      for (int cc = 0; cc < NCm; ++cc) {
+        const float v = sm.encR[(cc * M + ii) * M + jj];
+        sm.encR[(cc * M + ii) * M + jj] = R;
+        R = fmaf(exp2_acc(-sm.bl2[p] * (sm.anc[cc + 1] - sm.anc[cc])), R, v);
+      }
+      const float2 w = reinterpret_cast<const float2 *>(sm.W)[jj];
+      const FF Cp = ff_div(ff_add(FF{w.x, w.y}, FF{-R, 0.f}), sm.beta[p]);
+      sm.C[p] = Cp.hi + Cp.lo;
+    } else {
+      sm.C[p] = 0.f;
+    }
+  }
+  __syncthreads();
+  // pass 2: the features, from each chunk's entering state
+  if (act) {
+    for (int j = 0; j < M; ++j) S[j * NT + tid] = sm.encR[(c * M + i) * M + j];
+    walk(true);
+  }
+  __syncthreads();
+}
+
 // Per-thread state of one evaluation over the sorted features: the current
 // type i (its row alpha_i and mu_i in registers), the running sums of its
 // gradient, and the segment flush when the thread's range crosses into the
@@ -307,7 +433,7 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
   sm.bind(smem, a.carve);
   constexpr int AP = M + 4;
   const int Mrt = a.Mrt;
-  const int nb = BM == 0 ? 1 : Mrt;
+  const int nb = BM == 0 ? 1 : (BM == 1 ? Mrt : Mrt * Mrt);
   const int np = Mrt + Mrt * Mrt + nb;
   const int nupd = Mrt + Mrt * Mrt;
   const int tid = threadIdx.x, NT = NTC > 0 ? NTC : (int)blockDim.x;
@@ -364,7 +490,7 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     if (a.init == 1) {
       for (int p = tid; p < Mrt * Mrt; p += NT) {
         const int i = p / Mrt, j = p % Mrt;
-        sm.alpha[i * AP + j] = 0.5f * sm.beta[BM == 0 ? 0 : j] / (float)Mrt;
+        sm.alpha[i * AP + j] = 0.5f * sm.beta[BM == 0 ? 0 : (BM == 1 ? j : i * M + j)] / (float)Mrt;
       }
       for (int i = tid; i < Mrt; i += NT) sm.mu[i] = 0.5f * (float)max(sm.cnt[i], 1) / T;
     }
@@ -376,14 +502,19 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     }
     const EvG ev{tg, ug, wg};
     setup_chunks(NT, N, T, ev, sm.bnd, sm.anc);
-    prepare_states<M, 1, BM, false>(NT, ev, Mrt, sm);
+    if constexpr (BM != 2) prepare_states<M, 1, BM, false>(NT, ev, Mrt, sm);
     // thread ranges over the sorted features; an odd length keeps the
     // lanes' shared-memory float4 reads on distinct bank groups
     int L = (N + NT - 1) / NT;
     L = max(L | 1, 1);
     const XMap xm{L, NT};
-    if (XS) build_features<M, BM, true>(N, ev, Mrt, sm, sm.xs, xcap, xm);
-    else build_features<M, BM, false>(N, ev, Mrt, sm, Xg, xcap, xm);
+    if constexpr (BM == 2) {
+      if (XS) build_features_matrix<M, true>(N, T, ev, Mrt, sm, sm.xs, xcap, xm);
+      else build_features_matrix<M, false>(N, T, ev, Mrt, sm, Xg, xcap, xm);
+    } else {
+      if (XS) build_features<M, BM, true>(N, ev, Mrt, sm, sm.xs, xcap, xm);
+      else build_features<M, BM, false>(N, ev, Mrt, sm, Xg, xcap, xm);
+    }
     if (pipe) fence_proxy_async_global();  // this thread's feature stores -> the copy engine
     const int p0 = min(tid * L, N), p1 = min(p0 + L, N);
     int i0 = 0;
@@ -420,7 +551,7 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
         kahan_add(Ps, Pc, -T * sm.mu[p]);
       } else {
         const int qq = p - M, i = qq / M, j = qq % M;
-        kahan_add(Ps, Pc, -sm.alpha[i * AP + j] * sm.C[j]);
+        kahan_add(Ps, Pc, -sm.alpha[i * AP + j] * sm.C[BM == 2 ? i * M + j : j]);
       }
     }
     for (k = 0; k < a.max_iters; ++k) {
@@ -486,7 +617,7 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
           i = (p - M) / M; j = (p - M) % M; pc = Mrt + i * Mrt + j;
         }
         if (i >= Mrt || (j < M && j >= Mrt)) continue;
-        const float cj = (j == M) ? T : sm.C[j];
+        const float cj = (j == M) ? T : sm.C[BM == 2 ? i * M + j : j];
         const float g = xseg_sum<M>(i, j, sm) - cj;
         bad |= !isfinite(g);
         float &th = (j == M) ? sm.mu[i] : sm.alpha[i * AP + j];
@@ -524,7 +655,8 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     for (int p = tid; p < Mrt * Mrt; p += NT)
       a.alpha[(int64_t)b * Mrt * Mrt + p] = sm.alpha[(p / Mrt) * AP + (p % Mrt)];
     for (int i = tid; i < Mrt; i += NT) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];
-    for (int j = tid; j < nb; j += NT) a.beta[(int64_t)b * nb + j] = sm.beta[j];
+    for (int j = tid; j < nb; j += NT)
+      a.beta[(int64_t)b * nb + j] = sm.beta[BM == 2 ? (j / Mrt) * M + (j % Mrt) : j];
     if (tid == 0) {
       a.loglik[b] = ff_to_double(lnl_out);
       a.iters[b] = k;

@@ -74,8 +74,17 @@ __device__ void load_params(int b, int Mrt, const float *mu, const float *alpha,
     const int i = p / AP, j = p % AP;
     sm.alpha[p] = (i < Mrt && j < Mrt) ? alpha[(int64_t)b * Mrt * Mrt + i * Mrt + j] : 0.f;
   }
+  for (int j = threadIdx.x; j < M; j += blockDim.x) sm.mu[j] = j < Mrt ? mu[(int64_t)b * Mrt + j] : 0.f;
+  if (BM == 2) {  // matrix beta [i][j] (pitch M in shared memory; 1 in padding)
+    for (int p = threadIdx.x; p < M * M; p += blockDim.x) {
+      const int i = p / M, j = p % M;
+      const float bv = (i < Mrt && j < Mrt) ? beta[(int64_t)b * Mrt * Mrt + i * Mrt + j] : 1.f;
+      sm.beta[p] = bv;
+      sm.bl2[p] = bv * kLog2e;
+    }
+    return;
+  }
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
-    sm.mu[j] = j < Mrt ? mu[(int64_t)b * Mrt + j] : 0.f;
     const float bv = (j < nb) ? beta[(int64_t)b * nb + j] : 1.f;
     sm.beta[j] = bv;
     sm.bl2[j] = bv * kLog2e;

@@ -218,7 +218,9 @@ __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, 
 // counters of the feature pass share the same space); xcap > 0 places the
 // features in shared memory (xcap events x M floats).
 __host__ __device__ inline Carve make_carve_x(int M, int NT, int xcap, bool adam,
-                                              int pipe_steps = 0, int pipe_stages = 0) {
+                                              int pipe_steps = 0, int pipe_stages = 0,
+                                              bool matrix = false) {
+  const int MB = matrix ? M * M : M;  // beta, beta log2(e) and C: one per pair for matrix beta
   Carve c = {};
   int o = 0;
   const int AP = pitch4(M);
@@ -229,12 +231,12 @@ __host__ __device__ inline Carve make_carve_x(int M, int NT, int xcap, bool adam
   c.alpha = take(M * AP * 4);
   c.mu = take(M * 4);
   c.gm = take(M * 4);
-  c.beta = take(M * 4);
-  c.bl2 = take(M * 4);
+  c.beta = take(MB * 4);
+  c.bl2 = take(MB * 4);
   c.gb = take(M * 4);
   c.W = take(M * 8);
   c.cnt = take(M * 4);
-  c.C = take(M * 4);
+  c.C = take(MB * 4);
   c.dC = take(M * 4);
   c.endR = take(M * 4);
   c.endS = take(M * 4);

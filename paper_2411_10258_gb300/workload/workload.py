@@ -18,6 +18,8 @@ name what
      beta per window in {0.5, 1, 2}
 5    65,536 windows, M=32, counts log-uniform [100, 10000], 10 % carry one
      injected self-exciting component (alpha_kk = 0.9 beta, mu_k x 5)
+6    the shapes of workload 2 with the full decay matrix: beta_ij log-uniform
+     [0.5, 2] per window and pair, rho(alpha / beta) ~ U(0.2, 0.8)
 ==== ========================================================================
 
 Layout produced (what the C ABI consumes): CSR ``offsets`` int64[B+1],
@@ -253,6 +255,13 @@ def make_params(name: int, B: int | None = None, seed: int = BASE_SEED, beta: fl
         rho = rng.uniform(0.2, 0.8, size=B)
         mu, alpha = sample_params(rng, B, M, mode, betas, rho)
         counts = log_uniform_counts(rng, B, 500, 5000)
+    elif name == 6:
+        B = 4096 if B is None else B
+        M, mode = 16, 2
+        betas = np.exp(rng.uniform(np.log(0.5), np.log(2.0), size=(B, M * M)))
+        rho = rng.uniform(0.2, 0.8, size=B)
+        mu, alpha = sample_params(rng, B, M, mode, betas, rho)
+        counts = log_uniform_counts(rng, B, 200, 5000)
     elif name == 5:
         B = 65536 if B is None else B
         M, mode = 32, 0
