@@ -304,6 +304,20 @@ mdhp_status mdhp_init_train_step(mdhp_init_model *model, const void *features_bf
                                  const float *mu_target, const float *alpha_target, int32_t B,
                                  float lr, float weight_decay, float *loss_out, void *stream);
 
+/* The training step in two halves, for data-parallel training over several
+ * processes: mdhp_init_backward computes the loss and its gradient (into the
+ * model's gradient buffer, readable with mdhp_init_model_get(what = 1)) for
+ * this process's B windows; the caller averages the buffers over processes
+ * (an all-reduce of num_params floats) and writes the mean back with
+ * mdhp_init_set_grads; mdhp_init_apply then takes the AdamW step.
+ * mdhp_init_train_step = backward + apply. */
+mdhp_status mdhp_init_backward(mdhp_init_model *model, const void *features_bf16,
+                               const float *mu_cold, const float *beta, int32_t beta_stride,
+                               const float *mu_target, const float *alpha_target, int32_t B,
+                               float *loss_out, void *stream);
+mdhp_status mdhp_init_set_grads(mdhp_init_model *model, const float *src, void *stream);
+mdhp_status mdhp_init_apply(mdhp_init_model *model, float lr, float weight_decay, void *stream);
+
 /* Attach a trained model to a plan: mdhp_fit_batch with opts->init == 2 then
  * predicts the starting point with it (the plan does not own the model). */
 mdhp_status mdhp_plan_set_init_model(mdhp_plan *plan, mdhp_init_model *model);

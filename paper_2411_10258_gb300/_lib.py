@@ -72,6 +72,9 @@ SIGNATURES = [
     ("mdhp_init_predict", ctypes.c_int, [P, ctypes.POINTER(MdhpBatch), P, P, P, P]),
     ("mdhp_init_train_step", ctypes.c_int, [P, P, P, P, ctypes.c_int32, P, P, ctypes.c_int32,
                                             ctypes.c_float, ctypes.c_float, P, P]),
+    ("mdhp_init_backward", ctypes.c_int, [P, P, P, P, ctypes.c_int32, P, P, ctypes.c_int32, P, P]),
+    ("mdhp_init_set_grads", ctypes.c_int, [P, P, P]),
+    ("mdhp_init_apply", ctypes.c_int, [P, ctypes.c_float, ctypes.c_float, P]),
     ("mdhp_plan_set_init_model", ctypes.c_int, [P, P]),
     ("mdhp_last_error", ctypes.c_char_p, []),
     ("mdhp_version", ctypes.c_int32, []),

@@ -390,6 +390,40 @@ class InitModel:
             float(lr), float(weight_decay), _ptr(loss_out), _stream(stream)), "mdhp_init_train_step")
         return loss_out
 
+    def backward(self, feat, mu_cold, beta, mu_target, alpha_target, loss_out=None, stream=None):
+        """Loss and gradient of this process's windows (mdhp_init_backward); no update."""
+        B = feat.shape[0]
+        beta = beta.contiguous().float()
+        bstride = 1 if beta.numel() == B else self.M
+        if loss_out is None:
+            loss_out = torch.empty(1, dtype=torch.float32, device=feat.device)
+        _lib.check(self.lib.mdhp_init_backward(
+            self.h, _ptr(feat.contiguous()), _ptr(mu_cold.contiguous()), _ptr(beta), bstride,
+            _ptr(mu_target.contiguous().float()), _ptr(alpha_target.contiguous().float()), B,
+            _ptr(loss_out), _stream(stream)), "mdhp_init_backward")
+        return loss_out
+
+    def set_grads(self, grads: torch.Tensor, stream=None):
+        _lib.check(self.lib.mdhp_init_set_grads(self.h, _ptr(grads.contiguous().float()), _stream(stream)),
+                   "mdhp_init_set_grads")
+
+    def apply(self, lr=3e-4, weight_decay=5e-5, stream=None):
+        """AdamW step with the current gradient buffer (mdhp_init_apply)."""
+        _lib.check(self.lib.mdhp_init_apply(self.h, float(lr), float(weight_decay), _stream(stream)),
+                   "mdhp_init_apply")
+
+    def train_step_dp(self, feat, mu_cold, beta, mu_target, alpha_target, lr=3e-4, weight_decay=5e-5):
+        """Data-parallel step: local gradient, mean over the ranks of the default
+        process group, then AdamW on every rank (identical parameters after it)."""
+        from . import shard
+
+        loss = self.backward(feat, mu_cold, beta, mu_target, alpha_target)
+        g = self.get("grads")
+        shard.allreduce_mean_(g)
+        self.set_grads(g)
+        self.apply(lr, weight_decay)
+        return loss
+
     def attach(self, plan: "Plan"):
         """Use this model for FitOptions(init=2) fits of `plan`."""
         _lib.check(self.lib.mdhp_plan_set_init_model(plan.h, self.h), "mdhp_plan_set_init_model")

@@ -717,14 +717,14 @@ mdhp_status mdhp_init_predict(mdhp_init_model *p, const mdhp_batch *batch, const
   return MDHP_OK;
 }
 
-mdhp_status mdhp_init_train_step(mdhp_init_model *p, const void *features_bf16,
-                                 const float *mu_cold, const float *beta, int32_t beta_stride,
-                                 const float *mu_target, const float *alpha_target, int32_t B,
-                                 float lr, float weight_decay, float *loss_out, void *stream) {
+mdhp_status mdhp_init_backward(mdhp_init_model *p, const void *features_bf16,
+                               const float *mu_cold, const float *beta, int32_t beta_stride,
+                               const float *mu_target, const float *alpha_target, int32_t B,
+                               float *loss_out, void *stream) {
   if (!p || !features_bf16 || !mu_cold || !beta || !mu_target || !alpha_target)
-    return init_fail(MDHP_E_ARG, "mdhp_init_train_step: NULL argument");
-  if (B < 1 || B > p->max_batch) return init_fail(MDHP_E_ARG, "mdhp_init_train_step: B outside 1..max_batch");
-  if (beta_stride != 1 && beta_stride != p->M) return init_fail(MDHP_E_ARG, "mdhp_init_train_step: beta_stride");
+    return init_fail(MDHP_E_ARG, "mdhp_init_backward: NULL argument");
+  if (B < 1 || B > p->max_batch) return init_fail(MDHP_E_ARG, "mdhp_init_backward: B outside 1..max_batch");
+  if (beta_stride != 1 && beta_stride != p->M) return init_fail(MDHP_E_ARG, "mdhp_init_backward: beta_stride");
   cudaStream_t st = (cudaStream_t)stream;
   const __nv_bfloat16 *X = (const __nv_bfloat16 *)features_bf16;
   init_forward(p, X, B, st);
@@ -747,15 +747,41 @@ mdhp_status mdhp_init_train_step(mdhp_init_model *p, const void *features_bf16,
       k_relu_bwd<<<grid1(n), 256, 0, st>>>(p->dh[l - 1], p->h[l - 1], p->dhb[l - 1], n);
     }
   }
+  if (loss_out) cudaMemcpyAsync(loss_out, p->loss, 4, cudaMemcpyDeviceToDevice, st);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_init_set_grads(mdhp_init_model *p, const float *src, void *stream) {
+  if (!p || !src) return init_fail(MDHP_E_ARG, "mdhp_init_set_grads: NULL argument");
+  if (cudaMemcpyAsync(p->g, src, (size_t)p->nparams * 4, cudaMemcpyDeviceToDevice,
+                      (cudaStream_t)stream) != cudaSuccess)
+    return init_fail(MDHP_E_CUDA, cudaGetErrorString(cudaGetLastError()));
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_init_apply(mdhp_init_model *p, float lr, float weight_decay, void *stream) {
+  if (!p) return init_fail(MDHP_E_ARG, "mdhp_init_apply: NULL model");
+  cudaStream_t st = (cudaStream_t)stream;
   p->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)p->step), c2 = 1.f - powf(b2, (float)p->step);
   k_adamw<<<grid1(p->nparams), 256, 0, st>>>(p->w, p->g, p->m, p->v, p->wb, p->is_matrix,
                                               p->nparams, lr, b1, b2, 1e-8f, weight_decay, c1, c2);
-  if (loss_out) cudaMemcpyAsync(loss_out, p->loss, 4, cudaMemcpyDeviceToDevice, st);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
   return MDHP_OK;
+}
+
+mdhp_status mdhp_init_train_step(mdhp_init_model *p, const void *features_bf16,
+                                 const float *mu_cold, const float *beta, int32_t beta_stride,
+                                 const float *mu_target, const float *alpha_target, int32_t B,
+                                 float lr, float weight_decay, float *loss_out, void *stream) {
+  const mdhp_status s = mdhp_init_backward(p, features_bf16, mu_cold, beta, beta_stride, mu_target,
+                                           alpha_target, B, loss_out, stream);
+  if (s != MDHP_OK) return s;
+  return mdhp_init_apply(p, lr, weight_decay, stream);
 }
 
 }  // extern "C"

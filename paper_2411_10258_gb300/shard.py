@@ -7,7 +7,8 @@ iterations x events), not by window count: windows are taken longest first
 and each goes to the rank with the fewest events so far (the longest-
 processing-time rule), which keeps every rank within one window's events of
 the mean.  Collectives appear only around the data path: the max-over-ranks
-time of a timed region and the gather of per-window results to every rank.
+time of a timed region, the gather of per-window results to every rank, and
+the gradient mean of data-parallel training of the learned initializer.
 """
 from __future__ import annotations
 
@@ -43,6 +44,27 @@ def max_over_ranks(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def allreduce_mean_(t: torch.Tensor, group=None) -> torch.Tensor:
+    """In-place mean of `t` over the ranks of the process group (the gradient
+    exchange of data-parallel initializer training).  A gloo group reduces a
+    host copy of a device tensor.  No-op without an initialised group."""
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return t
+    world = dist.get_world_size(group)
+    if world == 1:
+        return t
+    if t.is_cuda and dist.get_backend(group) == "gloo":
+        h = t.detach().cpu()
+        dist.all_reduce(h, op=dist.ReduceOp.SUM, group=group)
+        t.copy_(h.to(t.device) / world)
+    else:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        t /= world
+    return t
 
 
 def gather_windows(local: torch.Tensor, idx_local, B: int) -> torch.Tensor:

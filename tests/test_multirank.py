@@ -35,7 +35,9 @@ def _rank(rank, world, port, counts, q):
                              torch.as_tensor(counts[mine], dtype=torch.float64)], dim=1)
         full = shard.gather_windows(local, mine, len(counts))
         tmax = shard.max_over_ranks(10.0 + rank)
-        q.put((rank, [p.tolist() for p in parts], full.numpy().tolist(), tmax))
+        g = torch.arange(5, dtype=torch.float32) * (rank + 1)  # rank r holds (r + 1) * [0..4]
+        shard.allreduce_mean_(g)
+        q.put((rank, [p.tolist() for p in parts], full.numpy().tolist(), tmax, g.tolist()))
     finally:
         dist.destroy_process_group()
 
@@ -73,7 +75,8 @@ def test_two_gloo_ranks():
         assert p.exitcode == 0
     res.sort()
     expect = np.stack([np.arange(37) * 2.0, counts.astype(np.float64)], axis=1)
-    for rank, parts, full, tmax in res:
+    for rank, parts, full, tmax, g in res:
         assert parts == res[0][1]
         np.testing.assert_array_equal(np.asarray(full), expect)
         assert tmax == 11.0
+        np.testing.assert_allclose(g, np.arange(5) * 1.5)  # mean of 1x and 2x
