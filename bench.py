@@ -46,10 +46,12 @@ def parse():
     ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 5, 6],
+    ap.add_argument("--workload", default="2", choices=["2", "3", "5", "6", "attack"],
                     help="2: fixed-iteration fits (default line); 5: warm vs cold fits to tolerance")
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--attack-windows", type=int, default=128,
+                    help="attacked (and as many normal) windows per combination (--workload attack)")
     ap.add_argument("--profile-step", action="store_true",
                     help="bracket the first timed step with cudaProfilerStart/Stop (for ncu "
                          "--replay-mode app-range: one fit's launches measured as one range)")
@@ -156,7 +158,7 @@ WORKLOAD6 = ("4096 windows x M=16, counts log-uniform[200,5000], beta_ij matrix 
 def make_inputs(args, rank):
     from paper_2411_10258_gb300.workload import workload
 
-    name = 6 if args.workload == 6 else 2
+    name = 6 if args.workload == '6' else 2
     bt = workload.make_workload(name, B=args.windows, seed=2024 + rank, beta=args.beta)
     return bt
 
@@ -311,7 +313,7 @@ def run_ours(args):
     peaks, src = measured_peaks()
     traffic = args.traffic
     if traffic is None and B == 4096 and M == 16 and args.iters == 200 and args.beta == 1.0 \
-            and args.workload == 2:
+            and args.workload == '2':
         traffic = FIT_DRAM_BYTES_4096xM16
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = fp32_peak_tflops(sm_count, float(peaks.get("sm_max_mhz", 2070.0)))
@@ -321,7 +323,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD6 if args.workload == 6 else WORKLOAD,
+            "config": {"workload": WORKLOAD6 if args.workload == '6' else WORKLOAD,
                        "windows_per_gpu": B, "M": M,
                        "events_per_gpu": int(bt.n_events), "iterations": args.iters,
                        "parallelism": f"windows sharded over {world} GPU(s), no collective",
@@ -465,6 +467,99 @@ def run_long_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def _auc(pos, neg):
+    """Area under the ROC curve of scores pos (attacked) vs neg (normal),
+    by the Mann-Whitney rank sum (ties counted half)."""
+    pos, neg = np.asarray(pos, dtype=np.float64), np.asarray(neg, dtype=np.float64)
+    allv = np.concatenate([pos, neg])
+    order = np.argsort(allv, kind="stable")
+    ranks = np.empty(len(allv))
+    ranks[order] = np.arange(1, len(allv) + 1)
+    for v in np.unique(allv):  # average ranks of ties
+        sel = allv == v
+        if sel.sum() > 1:
+            ranks[sel] = ranks[sel].mean()
+    return float((ranks[:len(pos)].sum() - len(pos) * (len(pos) + 1) / 2) / (len(pos) * len(neg)))
+
+
+def run_attacks(args):
+    """Separability of MDHP-GDS parameters between normal and attacked windows
+    (a synthetic analogue of the paper's CDF experiment): background windows
+    of workload-2 shape (M = 16, beta = 1, 1,000-3,000 events); half of each
+    group receive one time-exciting injection stream (each strategy with NPP
+    and ND candidates, and DRP) on a random message ID k; every window is
+    fitted by projected Adam to tol 1e-6; two scores of ID k (k random in
+    normal windows): the baseline share mu_k / (N_k / T) and the
+    self-excitation alpha_kk / beta.  Reports the AUC per combination."""
+    import torch
+
+    from paper_2411_10258_gb300 import DeviceBatch, FitOptions, Plan
+    from paper_2411_10258_gb300.workload import attacks, workload
+
+    dev = torch.device("cuda", 0)
+    M, n = 16, args.attack_windows
+    combos = [(sp, st) for sp in ("NPP", "ND") for st in attacks.STRATEGIES] + [("DRP", "DAM")]
+    rng = np.random.default_rng(77)
+    B = 2 * n * len(combos)
+    betas = np.ones((B, 1))
+    mu, alpha = workload.sample_params(rng, B, M, 0, betas, rng.uniform(0.2, 0.8, B))
+    counts = workload.log_uniform_counts(rng, B, 1000, 3000)
+    bg = workload.simulate(M, 0, mu, alpha, betas, counts, 7, 21)
+    ts, ids, Ts, ks, labels, combo_of = [], [], [], [], [], []
+    for c, (sp, st) in enumerate(combos):
+        for r in range(2 * n):
+            b = c * 2 * n + r
+            t, u, T, _ = bg.window(b)
+            k = int(rng.integers(M))
+            if r < n:  # attacked
+                a = attacks.sample(sp, st, rng)
+                t, u = attacks.inject(t, u, float(T), a, k)
+            ts.append(np.asarray(t, dtype=np.float32))
+            ids.append(np.asarray(u, dtype=np.int16))
+            Ts.append(max(float(T), float(np.float32(t[-1])) if len(t) else 0.0))
+            ks.append(k)
+            labels.append(r < n)
+            combo_of.append(c)
+    off = np.zeros(B + 1, dtype=np.int64)
+    np.cumsum([len(x) for x in ts], out=off[1:])
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    db = DeviceBatch(M, 0, up(off), up(np.concatenate(ts)), up(np.concatenate(ids)),
+                     up(np.asarray(Ts, dtype=np.float32)), None, int(np.diff(off).max()))
+    plan = Plan(M, 0, B, int(np.diff(off).max()))
+    beta = torch.ones(B, 1, device=dev)
+    mu_d = torch.zeros(B, M, device=dev)
+    al_d = torch.zeros(B, M, M, device=dev)
+    opts = FitOptions(optimizer=1, max_iters=2000, lr=1e-2, tol=1e-6, init=1)
+    plan.set_timing(True)
+    out = plan.fit(db, opts, mu_d, al_d, beta)
+    torch.cuda.synchronize()
+    ms = plan.last_fit_ms()
+    mu_h, al_h = mu_d.cpu().numpy(), al_d.cpu().numpy()
+    n_k = np.array([np.sum(x == k) for x, k in zip(ids, ks)], dtype=np.float64)
+    base_share = np.array([mu_h[b, ks[b]] * Ts[b] / max(n_k[b], 1.0) for b in range(B)])
+    self_exc = np.array([al_h[b, ks[b], ks[b]] for b in range(B)])
+    labels, combo_of = np.asarray(labels), np.asarray(combo_of)
+    res = {}
+    for c, (sp, st) in enumerate(combos):
+        sel = combo_of == c
+        pos, neg = sel & labels, sel & ~labels
+        res[f"{sp}/{st}"] = {"auc_mu_share": _auc(-base_share[pos], -base_share[neg]),
+                             "auc_alpha_kk": _auc(self_exc[pos], self_exc[neg]),
+                             "injected_mean": float(np.mean([len(ts[b]) for b in np.nonzero(pos)[0]])
+                                                    - np.mean(counts[pos]))}
+    st_bad = int((out["status"].cpu().numpy() != 0).sum())
+    line = {"metric": "AUC of MDHP-GDS parameters, attacked vs normal windows", "value": None,
+            "unit": "AUC", "n_gpus": 1, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": f"{B} windows, M=16, beta=1, 1,000-3,000 background events, "
+                                   f"{n} attacked + {n} normal per combination, Adam lr 1e-2 to tol 1e-6",
+                       "scores": "mu_k T / N_k (lower when injected events are not baseline) and "
+                                 "alpha_kk (self-excitation of the attacked ID)"},
+            "fit_ms": ms, "fits_per_s": B / (ms / 1000.0), "invalid_windows": st_bad,
+            "iters_median": float(np.median(out["iters"].cpu().numpy())), "auc": res}
+    line["value"] = float(np.mean([max(v["auc_mu_share"], v["auc_alpha_kk"]) for v in res.values()]))
+    print(json.dumps(line), flush=True)
+
+
 def run_warm_cold(args):
     """Workload 5: 65,536 windows (M = 32, counts log-uniform [100, 10000], 10 %
     with an injected self-exciting component), fitted to |dlnL| <= tol |lnL|
@@ -567,10 +662,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == 5:
+    elif args.workload == '5':
         run_warm_cold(args)
-    elif args.workload == 3:
+    elif args.workload == '3':
         run_long_learned(args)
+    elif args.workload == "attack":
+        run_attacks(args)
     else:  # 2, or 6 (the same with the full decay matrix)
         run_ours(args)
 
