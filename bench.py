@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="2", choices=["2", "3", "5", "6", "attack"],
+    ap.add_argument("--workload", default="2", choices=["2", "3", "5", "6", "attack", "lstm"],
                     help="2: fixed-iteration fits (default line); 5: warm vs cold fits to tolerance")
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--no-autotune", action="store_true")
@@ -560,6 +560,63 @@ def run_attacks(args):
     print(json.dumps(line), flush=True)
 
 
+def run_lstm(args):
+    """MDHP-LSTM cell, forward + backward over a batch of windows: 4,096
+    windows of 128 messages with 11 inputs each (the paper's SOME/IP window
+    shape: 10 fields and the time), H = 64, the windows' MDHP parameters with
+    M = 16 and a scalar beta, one output.  value = windows/s for forward +
+    backward; FLOP count of the gate, cell and output arithmetic."""
+    import torch
+
+    from paper_2411_10258_gb300 import MdhpLSTMFunction
+
+    dev = torch.device("cuda", 0)
+    B, L, D, H, M, O = 4096, 128, 11, 64, 16, 1
+    g = torch.Generator(device=dev).manual_seed(3)
+    r = lambda *s, lo=0.0, hi=1.0: (torch.rand(*s, generator=g, device=dev) * (hi - lo) + lo)
+    k = 1.0 / np.sqrt(H)
+    leaf = lambda t: t.requires_grad_(True)
+    x = leaf(r(B, L, D, lo=-1.0))
+    mu, alpha, beta = leaf(r(B, M, lo=0.1)), leaf(r(B, M, M, hi=0.05)), leaf(r(B, 1, lo=0.5, hi=2.0))
+    T = r(B, lo=5.0, hi=20.0)
+    W, U, b = leaf(r(4 * H, D, lo=-k, hi=k)), leaf(r(4 * H, H, lo=-k, hi=k)), leaf(r(4 * H, lo=-k, hi=k))
+    A, Bm, C = leaf(r(H, M * M, lo=-k, hi=k)), leaf(r(H, 1, lo=-k / 20, hi=k / 20)), leaf(r(H, M, lo=-k, hi=k))
+    Wy = leaf(r(O, H, lo=-k, hi=k))
+    dy = torch.ones(B, L, O, device=dev)
+
+    def step():
+        y = MdhpLSTMFunction.apply(x, mu, alpha, beta, T, W, U, b, A, Bm, C, Wy)
+        y.backward(dy)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    G = 4 * H
+    fwd = 2 * G * (D + H) + 10 * H + 2 * O * H           # per step and sequence
+    bwd = 2 * G * (D + H) + 2 * G * (D + H) + 20 * H + 4 * O * H  # dx, dh, and the weight sums
+    flops = float(B) * L * (fwd + bwd)
+    peaks, src = measured_peaks()
+    peak = fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count,
+                            float(peaks.get("sm_max_mhz", 2070.0)))
+    ach = flops / (ms / 1000.0) / 1e12
+    line = {"metric": "MDHP-LSTM forward+backward windows/s", "value": B / (ms / 1000.0),
+            "unit": "windows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{B} windows x {L} messages x {D} inputs, H={H}, M={M}, scalar beta, O={O}"},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "flops_per_step_sequence": fwd + bwd, "traffic": None,
+                         "kernel": "k_lstm_fwd / k_lstm_bwd (one CTA per sequence through time)"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_warm_cold(args):
     """Workload 5: 65,536 windows (M = 32, counts log-uniform [100, 10000], 10 %
     with an injected self-exciting component), fitted to |dlnL| <= tol |lnL|
@@ -668,6 +725,8 @@ def main():
         run_long_learned(args)
     elif args.workload == "attack":
         run_attacks(args)
+    elif args.workload == "lstm":
+        run_lstm(args)
     else:  # 2, or 6 (the same with the full decay matrix)
         run_ours(args)
 

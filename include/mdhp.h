@@ -432,6 +432,44 @@ mdhp_status mdhp_simulate(int32_t M, int32_t beta_mode, int32_t B, const double 
                           uint64_t first_window, float *t, int16_t *id, float *T_span,
                           int32_t *win_status, void *stream);
 
+/*
+ * MDHP-LSTM cell (the paper's MDHP-LSTM equation, Sec. "MDHP-LSTM"): an LSTM
+ * whose cell update is multiplied by a per-sequence Hawkes gate built from a
+ * window's fitted MDHP parameters,
+ *   hks = tanh(A vec(alpha) - Bm (beta T_span) + C mu)          [H]
+ *   i, f, o = sigmoid(W_{i,f,o} x_t + U_{i,f,o} h_{t-1} + b_{i,f,o})
+ *   g = tanh(W_c x_t + U_c h_{t-1} + b_c)
+ *   c_t = hks * (f * c_{t-1} + i * g),  h_t = o * tanh(c_t),  y_t = Wy h_t
+ * with h_{-1} = c_{-1} = 0 (step t consumes x_t and emits y_t: the paper
+ * writes x^{t-1} and Wy h^{t-1}).  FP32, device pointers, row-major:
+ *   x [B][L][D]; mu [B][M]; alpha [B][M][M]; beta [B][nb] (nb = 1 or M);
+ *   T_span [B]; W [4H][D], U [4H][H], b [4H] (gate rows i, f, g, o);
+ *   A [H][M*M], Bm [H][nb], C [H][M]; Wy [O][H].
+ * Forward outputs (all written): y [B][L][O]; and for the backward pass
+ * h_seq, c_seq [B][L][H], gates [B][L][4H] (activations), hks [B][H].
+ * Backward: gradients of sum(y * dy) with respect to x, every weight and the
+ * MDHP inputs (mu, alpha, beta); dW, dU, db, dA, dBm, dC, dWy are
+ * overwritten; dz_work [B][L][4H] and dpre_work [B][H] are scratch.
+ * Limits: H 1..256, D <= 3H, O <= 4H, M 1..64, L >= 1; MDHP_E_ARG otherwise.
+ */
+typedef struct {
+  int32_t B, L, D, H, M, nb, O;
+} mdhp_lstm_dims;
+
+mdhp_status mdhp_lstm_forward(const mdhp_lstm_dims *dims, const float *x, const float *mu,
+                              const float *alpha, const float *beta, const float *T_span,
+                              const float *W, const float *U, const float *b, const float *A,
+                              const float *Bm, const float *C, const float *Wy, float *y,
+                              float *h_seq, float *c_seq, float *gates, float *hks, void *stream);
+mdhp_status mdhp_lstm_backward(const mdhp_lstm_dims *dims, const float *x, const float *mu,
+                               const float *alpha, const float *beta, const float *T_span,
+                               const float *W, const float *U, const float *A, const float *Bm,
+                               const float *C, const float *Wy, const float *h_seq,
+                               const float *c_seq, const float *gates, const float *hks,
+                               const float *dy, float *dz_work, float *dpre_work, float *dx,
+                               float *dW, float *dU, float *db, float *dA, float *dBm, float *dC,
+                               float *dWy, float *dmu, float *dalpha, float *dbeta, void *stream);
+
 /* Text of the last error in this thread (static storage). */
 const char *mdhp_last_error(void);
 

@@ -27,6 +27,12 @@ class MdhpBatch(ctypes.Structure):
                 ("beta_mode", ctypes.c_int32), ("max_events", ctypes.c_int32)]
 
 
+class MdhpLstmDims(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("L", ctypes.c_int32), ("D", ctypes.c_int32),
+                ("H", ctypes.c_int32), ("M", ctypes.c_int32), ("nb", ctypes.c_int32),
+                ("O", ctypes.c_int32)]
+
+
 class MdhpFitOpts(ctypes.Structure):
     _fields_ = [("optimizer", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("fit_beta", ctypes.c_int32), ("patience", ctypes.c_int32),
@@ -76,6 +82,8 @@ SIGNATURES = [
     ("mdhp_init_set_grads", ctypes.c_int, [P, P, P]),
     ("mdhp_init_apply", ctypes.c_int, [P, ctypes.c_float, ctypes.c_float, P]),
     ("mdhp_plan_set_init_model", ctypes.c_int, [P, P]),
+    ("mdhp_lstm_forward", ctypes.c_int, [ctypes.POINTER(MdhpLstmDims)] + [P] * 18),
+    ("mdhp_lstm_backward", ctypes.c_int, [ctypes.POINTER(MdhpLstmDims)] + [P] * 30),
     ("mdhp_last_error", ctypes.c_char_p, []),
     ("mdhp_version", ctypes.c_int32, []),
 ]

@@ -427,3 +427,65 @@ class InitModel:
     def attach(self, plan: "Plan"):
         """Use this model for FitOptions(init=2) fits of `plan`."""
         _lib.check(self.lib.mdhp_plan_set_init_model(plan.h, self.h), "mdhp_plan_set_init_model")
+
+
+class MdhpLSTMFunction(torch.autograd.Function):
+    """The MDHP-LSTM cell over whole sequences (mdhp_lstm_forward /
+    mdhp_lstm_backward): inputs x [B, L, D], the windows' fitted MDHP
+    parameters mu [B, M], alpha [B, M, M], beta [B, nb] and T_span [B], and
+    the weights W [4H, D], U [4H, H], b [4H], A [H, M*M], Bm [H, nb],
+    C [H, M], Wy [O, H]; returns y [B, L, O].  Gradients flow to x, the
+    weights and (mu, alpha, beta); T_span gets none."""
+
+    @staticmethod
+    def forward(ctx, x, mu, alpha, beta, T, W, U, b, A, Bm, C, Wy):
+        lib = _lib.load()
+        c32 = lambda t: t.detach().contiguous().float()
+        x, mu, alpha, beta, T, W, U, b, A, Bm, C, Wy = map(c32, (x, mu, alpha, beta, T, W, U, b, A, Bm, C, Wy))
+        Bn, L, D = x.shape
+        H, M, O = U.shape[1], mu.shape[1], Wy.shape[0]
+        beta = beta.reshape(Bn, -1)
+        dims = _lib.MdhpLstmDims(Bn, L, D, H, M, beta.shape[1], O)
+        f32 = dict(dtype=torch.float32, device=x.device)
+        y = torch.empty(Bn, L, O, **f32)
+        hs, cs = torch.empty(Bn, L, H, **f32), torch.empty(Bn, L, H, **f32)
+        gates, hks = torch.empty(Bn, L, 4 * H, **f32), torch.empty(Bn, H, **f32)
+        _lib.check(lib.mdhp_lstm_forward(ctypes.byref(dims), *map(_ptr, (x, mu, alpha, beta, T, W, U, b, A, Bm,
+                                                                          C, Wy, y, hs, cs, gates, hks)),
+                                         _stream()), "mdhp_lstm_forward")
+        ctx.dims = (Bn, L, D, H, M, beta.shape[1], O)
+        ctx.save_for_backward(x, mu, alpha, beta, T, W, U, A, Bm, C, Wy, hs, cs, gates, hks)
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        lib = _lib.load()
+        x, mu, alpha, beta, T, W, U, A, Bm, C, Wy, hs, cs, gates, hks = ctx.saved_tensors
+        Bn, L, D, H, M, nb, O = ctx.dims
+        dims = _lib.MdhpLstmDims(Bn, L, D, H, M, nb, O)
+        dy = dy.contiguous().float()
+        z = lambda *shape: torch.empty(*shape, dtype=torch.float32, device=x.device)
+        dz, dpre = z(Bn, L, 4 * H), z(Bn, H)
+        dx, dW, dU, db = z(Bn, L, D), z(4 * H, D), z(4 * H, H), z(4 * H)
+        dA, dBm, dC, dWy = z(H, M * M), z(H, nb), z(H, M), z(max(O, 1), H)
+        dmu, dalpha, dbeta = z(Bn, M), z(Bn, M, M), z(Bn, nb)
+        _lib.check(lib.mdhp_lstm_backward(ctypes.byref(dims), *map(_ptr, (
+            x, mu, alpha, beta, T, W, U, A, Bm, C, Wy, hs, cs, gates, hks, dy, dz, dpre, dx, dW, dU, db,
+            dA, dBm, dC, dWy, dmu, dalpha, dbeta)), _stream()), "mdhp_lstm_backward")
+        return dx, dmu, dalpha, dbeta, None, dW, dU, db, dA, dBm, dC, dWy[:O]
+
+
+class MdhpLSTM(torch.nn.Module):
+    """MDHP-LSTM cell with its own weights (uniform +-1/sqrt(H) initialisation)."""
+
+    def __init__(self, D: int, H: int, M: int, nb: int = 1, O: int = 1, seed: int = 0):
+        super().__init__()
+        g = torch.Generator().manual_seed(seed)
+        k = 1.0 / np.sqrt(H)
+        u = lambda *shape: torch.nn.Parameter((torch.rand(*shape, generator=g) * 2 - 1) * k)
+        self.W, self.U, self.b = u(4 * H, D), u(4 * H, H), u(4 * H)
+        self.A, self.Bm, self.C, self.Wy = u(H, M * M), u(H, nb), u(H, M), u(O, H)
+
+    def forward(self, x, mu, alpha, beta, T_span):
+        return MdhpLSTMFunction.apply(x, mu, alpha, beta, T_span, self.W, self.U, self.b, self.A,
+                                      self.Bm, self.C, self.Wy)
