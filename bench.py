@@ -613,7 +613,7 @@ def run_lstm(args):
             "config": {"workload": f"{B} windows x {L} messages x {D} inputs, H={H}, M={M}, scalar beta, O={O}"},
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                          "flops_per_step_sequence": fwd + bwd, "traffic": None,
-                         "kernel": "k_lstm_fwd / k_lstm_bwd (one CTA per sequence through time)"}}
+                         "kernel": "k_lstm_fwd_s / k_lstm_bwd_s (S sequences per CTA through time)"}}
     print(json.dumps(line), flush=True)
 
 

@@ -15,6 +15,7 @@
 // the gradient of the Hawkes gate.  The weight gradients are row sums of
 // outer products, sum_r a_r^T b_r over the B*L steps, by a split reduction.
 #include <cstdint>
+#include <cstdlib>
 #include <cstdio>
 
 #include "mdhp.h"
@@ -160,6 +161,306 @@ __global__ void __launch_bounds__(1024) k_lstm_bwd(LstmBwd a) {
   if (r < H) a.dpre[(int64_t)bq * H + r] = dhks * (1.f - kh * kh);
 }
 
+// S sequences per CTA.  Forward: thread r keeps S accumulators of gate row
+// r, so each staged weight is read once per step for S sequences and the two
+// barriers of a step serve S sequences.  The matvec operands x_t and h_{t-1}
+// are [unit][SP] (SP = S + 4: one 16-byte load gives four sequences, and the
+// padding spreads the element-wise writes over the banks); the cell state and
+// Hawkes gate are [sequence][unit], so the element-wise phase runs with the
+// unit index fastest and its global loads and stores coalesce.  The input of
+// step t + 1 is fetched during the element-wise phase of step t.  y = Wy h is
+// left to k_lstm_out: it does not feed the recursion.
+template <int S>
+__global__ void __launch_bounds__(1024) k_lstm_fwd_s(LstmFwd a) {
+  constexpr int SP = S + 4;
+  extern __shared__ __align__(16) float sm[];
+  const int H = a.H, D = a.D, G = 4 * H, ZP = G + 1, r = threadIdx.x, nt = blockDim.x;
+  const int s0 = blockIdx.x * S;
+  float *xs = sm;               // [2][D][SP]  x_t in buffer t & 1
+  float *h = xs + 2 * D * SP;   // [H][SP]     h_{t-1}
+  float *c = h + H * SP;        // [S][H]      c_{t-1}
+  float *kh = c + S * H;        // [S][H]      Hawkes gate
+  float *z = kh + S * H;        // [S][ZP]     gate activations of step t
+  float *WT = z + S * ZP;       // [D][G]      (staged)
+  float *UT = WT + D * G;       // [H][G]
+  if (a.staged) {
+    for (int p = r; p < G * D; p += nt) WT[(p % D) * G + p / D] = a.W[p];
+    for (int p = r; p < G * H; p += nt) UT[(p % H) * G + p / H] = a.U[p];
+  }
+  const int MM = a.M * a.M;
+  for (int p = r; p < S * H; p += nt) {
+    const int s = p / H, j = p % H, q = s0 + s;
+    float v = 0.f;
+    if (q < a.B) {
+      float acc = 0.f;
+      for (int k = 0; k < MM; ++k) acc = fmaf(a.A[(int64_t)j * MM + k], a.alpha[(int64_t)q * MM + k], acc);
+      for (int k = 0; k < a.nb; ++k)
+        acc = fmaf(-a.Bm[(int64_t)j * a.nb + k], a.beta[(int64_t)q * a.nb + k] * a.T[q], acc);
+      for (int k = 0; k < a.M; ++k) acc = fmaf(a.C[(int64_t)j * a.M + k], a.mu[(int64_t)q * a.M + k], acc);
+      v = tanhf(acc);
+      a.hks[(int64_t)q * H + j] = v;
+    }
+    kh[p] = v;
+    c[p] = 0.f;
+    h[j * SP + s] = 0.f;
+  }
+  for (int p = r; p < S * D; p += nt) {
+    const int s = p / D, d = p % D, q = s0 + s;
+    xs[d * SP + s] = q < a.B ? a.x[(int64_t)q * a.L * D + d] : 0.f;
+  }
+  __syncthreads();
+  const float br = r < G ? a.b[r] : 0.f;
+  const bool tanh_row = r >= 2 * H && r < 3 * H;
+  for (int t = 0; t < a.L; ++t) {
+    const float *xc = xs + (t & 1) * D * SP;
+    if (r < G) {
+      float acc[S];
+#pragma unroll
+      for (int e = 0; e < S; ++e) acc[e] = br;
+      for (int d = 0; d < D; ++d) {
+        const float w = a.staged ? WT[d * G + r] : a.W[(int64_t)r * D + d];
+#pragma unroll
+        for (int e = 0; e < S; e += 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(xc + d * SP + e);
+          acc[e] = fmaf(w, v.x, acc[e]);
+          acc[e + 1] = fmaf(w, v.y, acc[e + 1]);
+          acc[e + 2] = fmaf(w, v.z, acc[e + 2]);
+          acc[e + 3] = fmaf(w, v.w, acc[e + 3]);
+        }
+      }
+#pragma unroll 4
+      for (int k = 0; k < H; ++k) {
+        const float w = a.staged ? UT[k * G + r] : a.U[(int64_t)r * H + k];
+#pragma unroll
+        for (int e = 0; e < S; e += 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(h + k * SP + e);
+          acc[e] = fmaf(w, v.x, acc[e]);
+          acc[e + 1] = fmaf(w, v.y, acc[e + 1]);
+          acc[e + 2] = fmaf(w, v.z, acc[e + 2]);
+          acc[e + 3] = fmaf(w, v.w, acc[e + 3]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < S; ++e) {
+        const float v = tanh_row ? tanhf(acc[e]) : sigm(acc[e]);
+        z[e * ZP + r] = v;
+        if (s0 + e < a.B) a.gates[((int64_t)(s0 + e) * a.L + t) * G + r] = v;
+      }
+    }
+    __syncthreads();
+    for (int p = r; p < S * H; p += nt) {
+      const int s = p / H, j = p % H, q = s0 + s;
+      const float *zs = z + s * ZP;
+      const float cn = kh[p] * fmaf(zs[H + j], c[p], zs[j] * zs[2 * H + j]);
+      const float hn = zs[3 * H + j] * tanhf(cn);
+      c[p] = cn;
+      h[j * SP + s] = hn;
+      if (q < a.B) {
+        const int64_t o = ((int64_t)q * a.L + t) * H + j;
+        a.cs[o] = cn;
+        a.hs[o] = hn;
+      }
+    }
+    if (t + 1 < a.L) {
+      float *xn = xs + ((t + 1) & 1) * D * SP;
+      for (int p = r; p < S * D; p += nt) {
+        const int s = p / D, d = p % D, q = s0 + s;
+        xn[d * SP + s] = q < a.B ? a.x[((int64_t)q * a.L + t + 1) * D + d] : 0.f;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// y[r][o] = sum_j Wy[o][j] h[r][j] over the R = B L rows of h_seq: one warp
+// per row, lanes over j, a shuffle reduction per output.
+__global__ void k_lstm_out(const float *hs, const float *Wy, int64_t R, int H, int O, float *y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w0; row < R; row += nw) {
+    const float *hr = hs + row * H;
+    for (int o = 0; o < O; ++o) {
+      float acc = 0.f;
+      for (int j = lane; j < H; j += 32) acc = fmaf(Wy[(int64_t)o * H + j], hr[j], acc);
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+      if (lane == 0) y[row * O + o] = acc;
+    }
+  }
+}
+
+// Backward through time, S sequences per CTA.  The element-wise phase runs
+// with the unit index fastest over [sequence][unit] state (coalesced global
+// loads of the saved gates and cell states) and writes the gate gradients dz
+// both to global memory (for the weight-gradient reduction) and, transposed,
+// to dzT [G][SP].  The matvec phase computes [dh_{t-1}; dx_t] = [U | W]^T dz
+// with thread (u, group) owning GW sequences of output unit u: one weight
+// load and GW/4 16-byte loads of dzT feed GW FMAs.
+template <int S>
+__global__ void __launch_bounds__(1024) k_lstm_bwd_s(LstmBwd a) {
+  constexpr int SP = S + 4, GW = S >= 16 ? 8 : 4;
+  extern __shared__ __align__(16) float sm[];
+  const int H = a.H, D = a.D, G = 4 * H, HD = H + D, r = threadIdx.x, nt = blockDim.x;
+  const int s0 = blockIdx.x * S;
+  float *dzT = sm;               // [G][SP]
+  float *dh = dzT + G * SP;      // [S][H]  dh_t from later steps
+  float *dcn = dh + S * H;       // [S][H]  dc_t from step t + 1
+  float *dhk = dcn + S * H;      // [S][H]  d hks accumulated over steps
+  float *kh = dhk + S * H;       // [S][H]
+  float *V = kh + S * H;         // [G][HD] rows of [U | W] (staged)
+  if (a.staged)
+    for (int p = r; p < G * HD; p += nt) {
+      const int g = p / HD, u = p % HD;
+      V[p] = u < H ? a.U[(int64_t)g * H + u] : a.W[(int64_t)g * D + (u - H)];
+    }
+  for (int p = r; p < S * H; p += nt) {
+    const int s = p / H, j = p % H, q = s0 + s;
+    dh[p] = 0.f;
+    dcn[p] = 0.f;
+    dhk[p] = 0.f;
+    kh[p] = q < a.B ? a.hks[(int64_t)q * H + j] : 0.f;
+  }
+  __syncthreads();
+  const int items = HD * (S / GW);
+  for (int t = a.L - 1; t >= 0; --t) {
+    for (int p = r; p < S * H; p += nt) {
+      const int s = p / H, j = p % H, q = s0 + s;
+      if (q >= a.B) {
+        dzT[j * SP + s] = dzT[(H + j) * SP + s] = dzT[(2 * H + j) * SP + s] = dzT[(3 * H + j) * SP + s] = 0.f;
+        continue;
+      }
+      const int64_t row = (int64_t)q * a.L + t;
+      float dht = dh[p];
+      for (int k = 0; k < a.O; ++k) dht = fmaf(a.Wy[(int64_t)k * H + j], a.dy[row * a.O + k], dht);
+      const float *gr = a.gates + row * G;
+      const float ig = gr[j], fg = gr[H + j], gg = gr[2 * H + j], og = gr[3 * H + j];
+      const float cv = a.cs[row * H + j];
+      const float cp = t > 0 ? a.cs[(row - 1) * H + j] : 0.f;
+      const float tc = tanhf(cv);
+      const float dc = fmaf(dht * og, 1.f - tc * tc, dcn[p]);
+      dhk[p] = fmaf(dc, fmaf(fg, cp, ig * gg), dhk[p]);
+      const float din = dc * kh[p];
+      const float zi = din * gg * ig * (1.f - ig);
+      const float zf = din * cp * fg * (1.f - fg);
+      const float zg = din * ig * (1.f - gg * gg);
+      const float zo = dht * tc * og * (1.f - og);
+      dzT[j * SP + s] = zi;
+      dzT[(H + j) * SP + s] = zf;
+      dzT[(2 * H + j) * SP + s] = zg;
+      dzT[(3 * H + j) * SP + s] = zo;
+      float *dzr = a.dz + row * G;
+      dzr[j] = zi;
+      dzr[H + j] = zf;
+      dzr[2 * H + j] = zg;
+      dzr[3 * H + j] = zo;
+      dcn[p] = din * fg;
+    }
+    __syncthreads();
+    for (int it = r; it < items; it += nt) {
+      const int u = it % HD, sb = (it / HD) * GW;
+      float acc[GW];
+#pragma unroll
+      for (int e = 0; e < GW; ++e) acc[e] = 0.f;
+#pragma unroll 4
+      for (int g = 0; g < G; ++g) {
+        const float w = a.staged ? V[g * HD + u]
+                                 : (u < H ? a.U[(int64_t)g * H + u] : a.W[(int64_t)g * D + (u - H)]);
+#pragma unroll
+        for (int e = 0; e < GW; e += 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(dzT + g * SP + sb + e);
+          acc[e] = fmaf(w, v.x, acc[e]);
+          acc[e + 1] = fmaf(w, v.y, acc[e + 1]);
+          acc[e + 2] = fmaf(w, v.z, acc[e + 2]);
+          acc[e + 3] = fmaf(w, v.w, acc[e + 3]);
+        }
+      }
+      if (u < H) {
+#pragma unroll
+        for (int e = 0; e < GW; ++e) dh[(sb + e) * H + u] = acc[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < GW; ++e)
+          if (s0 + sb + e < a.B) a.dx[((int64_t)(s0 + sb + e) * a.L + t) * D + (u - H)] = acc[e];
+      }
+    }
+    __syncthreads();
+  }
+  for (int p = r; p < S * H; p += nt) {
+    const int s = p / H, j = p % H, q = s0 + s;
+    if (q < a.B) a.dpre[(int64_t)q * H + j] = dhk[p] * (1.f - kh[p] * kh[p]);
+  }
+}
+
+// Weight gradients of the gates in one pass over dz:
+//   dW[g][d] += sum_r dz[r][g] x[r][d],  dU[g][k] += sum_r dz[r][g] h_{r-1}[k],
+//   db[g] += sum_r dz[r][g]
+// i.e. out[g][q] = sum_r dz[r][g] Bc[r][q] with Bc[r] = [x_r, h_{r-1}, 1]
+// (h_{r-1} = 0 at the first step of a sequence).  A CTA owns a 64 x 80 tile
+// of (g, q) over a chunk of rows, staged 32 rows at a time; thread (tg, tq)
+// keeps a 4 x 5 register tile.  Chunks meet in the output by atomic adds.
+constexpr int kWgG = 64, kWgQ = 80, kWgK = 32;
+__global__ void __launch_bounds__(256) k_lstm_wgrad(const float *dz, const float *x, const float *hs,
+                                                    int64_t R, int L, int D, int H, int64_t rows_per,
+                                                    float *dW, float *dU, float *db) {
+  __shared__ __align__(16) float As[kWgK][kWgG];
+  __shared__ float Bs[kWgK][kWgQ + 1];
+  const int G = 4 * H, Q = D + H + 1, tid = threadIdx.x;
+  const int tg = tid & 15, tq = tid >> 4;
+  const int g0 = blockIdx.x * kWgG, q0 = blockIdx.y * kWgQ;
+  const int64_t r0 = blockIdx.z * rows_per, r1 = r0 + rows_per < R ? r0 + rows_per : R;
+  float acc[4][5];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[i][k] = 0.f;
+  for (int64_t rb = r0; rb < r1; rb += kWgK) {
+    for (int e = tid; e < kWgK * kWgG / 4; e += 256) {
+      const int rr = e / (kWgG / 4), c4 = (e % (kWgG / 4)) * 4;
+      const int64_t rw = rb + rr;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rw < r1 && g0 + c4 < G) v = *reinterpret_cast<const float4 *>(dz + rw * G + g0 + c4);
+      *reinterpret_cast<float4 *>(&As[rr][c4]) = v;
+    }
+    for (int e = tid; e < kWgK * kWgQ; e += 256) {
+      const int rr = e / kWgQ, cc = e % kWgQ, q = q0 + cc;
+      const int64_t rw = rb + rr;
+      float v = 0.f;
+      if (rw < r1 && q < Q) {
+        if (q < D) v = x[rw * D + q];
+        else if (q < D + H) v = (rw % L) ? hs[(rw - 1) * H + (q - D)] : 0.f;
+        else v = 1.f;
+      }
+      Bs[rr][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kWgK; ++k) {
+      const float4 av = *reinterpret_cast<const float4 *>(&As[k][tg * 4]);
+      const float a4[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const float bv = Bs[k][tq * 5 + c];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i][c] = fmaf(a4[i], bv, acc[i][c]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int g = g0 + tg * 4 + i;
+    if (g >= G) continue;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const int q = q0 + tq * 5 + c;
+      if (q < D) atomicAdd(&dW[(int64_t)g * D + q], acc[i][c]);
+      else if (q < D + H) atomicAdd(&dU[(int64_t)g * H + (q - D)], acc[i][c]);
+      else if (q == D + H) atomicAdd(&db[g], acc[i][c]);
+    }
+  }
+}
+
 // out[p][q] (+)= scale * sum_{r < R} A(r, p) B(r, q), A(r, p) = A[r * lda + p],
 // B(r, q) = B[r * ldb + q] (or B[(r - 1) * ldb + q] with row r % L == 0 zero
 // when shift_L > 0: h_{t-1}); B == nullptr means B(r, q) = 1 (row sums).
@@ -222,6 +523,93 @@ int max_smem() {
   return v;
 }
 
+int num_sms() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return v;
+}
+
+// Dynamic shared memory of the S-sequence kernels (S = 1: the one-sequence
+// kernels), with the gate weights staged when they fit.
+int fwd_smem(int S, int D, int H, bool staged) {
+  const int G = 4 * H, SP = S + 4;
+  const int base = S == 1 ? (D + 2 * H + G + H) * 4 : (2 * D * SP + H * SP + 2 * S * H + S * (G + 1)) * 4;
+  return base + (staged ? (D + H) * G * 4 : 0);
+}
+int bwd_smem(int S, int D, int H, bool staged) {
+  const int G = 4 * H, SP = S + 4;
+  const int base = S == 1 ? (H + G) * 4 : (G * SP + 4 * S * H) * 4;
+  return base + (staged ? (D + H) * G * 4 : 0);
+}
+
+template <typename K>
+int resident(K kernel, int threads, int smem) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) n = 0;
+  return n;
+}
+
+// Sequences per CTA: the S in {1, 4, 8, 16} that minimises waves x (S + 8),
+// ties to the larger S.  A wave's time is modelled as a fixed part (barriers,
+// the latency of each step's dependent chain, weight staging) worth about
+// eight sequences' arithmetic plus a part linear in S; on GB300 at H = 64,
+// D = 11 the measured fwd+bwd times for S = 1, 4, 8, 16 over 4,096
+// sequences were 15.9, 11.2, 10.8 and 10.8 ms.  Both passes use the same S;
+// the forward kernel's residency decides.  MDHP_LSTM_SEQ_PER_CTA overrides
+// the choice.
+int pick_seq_per_cta(int B, int D, int H) {
+  if (const char *e = getenv("MDHP_LSTM_SEQ_PER_CTA")) {
+    const int v = atoi(e);
+    if (v == 1 || v == 4 || v == 8 || v == 16) return v;
+  }
+  const int G = 4 * H, threads = (G + 31) / 32 * 32, lim = max_smem();
+  int best = 1;
+  double best_cost = 1e300;
+  for (int S : {1, 4, 8, 16}) {
+    int smem = fwd_smem(S, D, H, true);
+    if (smem > lim) smem = fwd_smem(S, D, H, false);
+    if (smem > lim) continue;
+    int res = 0;
+    switch (S) {
+      case 1: res = resident(k_lstm_fwd, threads, smem); break;
+      case 4: res = resident(k_lstm_fwd_s<4>, threads, smem); break;
+      case 8: res = resident(k_lstm_fwd_s<8>, threads, smem); break;
+      default: res = resident(k_lstm_fwd_s<16>, threads, smem); break;
+    }
+    if (res < 1) continue;
+    const int64_t blocks = ((int64_t)B + S - 1) / S, slots = (int64_t)res * num_sms();
+    const double cost = (double)((blocks + slots - 1) / slots) * (S + 8);
+    if (cost <= best_cost) {
+      best_cost = cost;
+      best = S;
+    }
+  }
+  return best;
+}
+
+template <int S>
+void launch_fwd(const LstmFwd &a0, int threads, cudaStream_t st) {
+  LstmFwd a = a0;
+  a.staged = fwd_smem(S, a.D, a.H, true) <= max_smem() ? 1 : 0;
+  const int smem = fwd_smem(S, a.D, a.H, a.staged);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_lstm_fwd_s<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_lstm_fwd_s<S><<<(a.B + S - 1) / S, threads, smem, st>>>(a);
+}
+
+template <int S>
+void launch_bwd(const LstmBwd &a0, int threads, cudaStream_t st) {
+  LstmBwd a = a0;
+  a.staged = bwd_smem(S, a.D, a.H, true) <= max_smem() ? 1 : 0;
+  const int smem = bwd_smem(S, a.D, a.H, a.staged);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_lstm_bwd_s<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_lstm_bwd_s<S><<<(a.B + S - 1) / S, threads, smem, st>>>(a);
+}
+
 mdhp_status check_dims(const mdhp_lstm_dims *d) {
   if (!d) return MDHP_E_ARG;
   if (d->B < 0 || d->L < 1 || d->D < 1 || d->H < 1 || d->H > 256 || d->M < 1 || d->M > 64 ||
@@ -261,15 +649,27 @@ extern "C" mdhp_status mdhp_lstm_forward(const mdhp_lstm_dims *d, const float *x
     return MDHP_E_ARG;
   }
   const int G = 4 * d->H;
-  const int base = (d->D + 2 * d->H + G + d->H) * 4;
-  const int full = base + (d->D + d->H) * G * 4;
-  const int staged = full <= max_smem() ? 1 : 0;
-  const int smem = staged ? full : base;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_lstm_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  LstmFwd a{d->B, d->L, d->D, d->H, d->M, d->nb, d->O, staged, x, mu, alpha, beta, T_span, W, U, b, A,
-            Bm, C, Wy, y, h_seq, c_seq, gates, hks};
   const int threads = (G + 31) / 32 * 32;
-  k_lstm_fwd<<<d->B, threads, smem, (cudaStream_t)stream>>>(a);
+  LstmFwd a{d->B, d->L, d->D, d->H, d->M, d->nb, d->O, 0, x, mu, alpha, beta, T_span, W, U, b, A,
+            Bm, C, Wy, y, h_seq, c_seq, gates, hks};
+  cudaStream_t st = (cudaStream_t)stream;
+  const int S = pick_seq_per_cta(d->B, d->D, d->H);
+  if (S > 1) {
+    if (S == 4) launch_fwd<4>(a, threads, st);
+    else if (S == 8) launch_fwd<8>(a, threads, st);
+    else launch_fwd<16>(a, threads, st);
+    if (d->O > 0) {
+      const int64_t R = (int64_t)d->B * d->L;
+      const int64_t want = (R + 7) / 8;
+      const int blocks = (int)(want < (int64_t)num_sms() * 16 ? want : (int64_t)num_sms() * 16);
+      k_lstm_out<<<blocks, 256, 0, st>>>(h_seq, Wy, R, d->H, d->O, y);
+    }
+    return launched("k_lstm_fwd_s / k_lstm_out");
+  }
+  a.staged = fwd_smem(1, d->D, d->H, true) <= max_smem() ? 1 : 0;
+  const int smem = fwd_smem(1, d->D, d->H, a.staged);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_lstm_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_lstm_fwd<<<d->B, threads, smem, st>>>(a);
   return launched("k_lstm_fwd");
 }
 
@@ -300,14 +700,19 @@ extern "C" mdhp_status mdhp_lstm_backward(
   cudaMemsetAsync(dC, 0, (size_t)H * M * 4, st);
   cudaMemsetAsync(dWy, 0, (size_t)(O > 0 ? O : 1) * H * 4, st);
   if (d->B == 0) return launched("mdhp_lstm_backward");
-  const int base = (H + G) * 4;
-  const int full = base + (D + H) * G * 4;
-  const int staged = full <= max_smem() ? 1 : 0;
-  const int smem = staged ? full : base;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_lstm_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  LstmBwd a{d->B, d->L, D, H, O, staged, W, U, Wy, h_seq, c_seq, gates, hks, dy, dz_work, dpre_work, dx};
   const int threads = (G + 31) / 32 * 32;
-  k_lstm_bwd<<<d->B, threads, smem, st>>>(a);
+  LstmBwd a{d->B, d->L, D, H, O, 0, W, U, Wy, h_seq, c_seq, gates, hks, dy, dz_work, dpre_work, dx};
+  switch (pick_seq_per_cta(d->B, D, H)) {
+    case 4: launch_bwd<4>(a, threads, st); break;
+    case 8: launch_bwd<8>(a, threads, st); break;
+    case 16: launch_bwd<16>(a, threads, st); break;
+    default: {
+      a.staged = bwd_smem(1, D, H, true) <= max_smem() ? 1 : 0;
+      const int smem = bwd_smem(1, D, H, a.staged);
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k_lstm_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      k_lstm_bwd<<<d->B, threads, smem, st>>>(a);
+    }
+  }
   mdhp_status s = launched("k_lstm_bwd");
   if (s != MDHP_OK) return s;
   const int64_t R = (int64_t)d->B * d->L;
@@ -317,9 +722,16 @@ extern "C" mdhp_status mdhp_lstm_backward(
     dim3 grid((Q + 15) / 16, (P + 15) / 16, (unsigned)split);
     k_atb<<<grid, 256, 0, st>>>(Ap, lda, Bp, ldb, P, Q, rows, shift, scale, out);
   };
-  atb(dz_work, G, x, D, G, D, R, 0, 1.f, dW);          // dW = sum_r dz_r^T x_r
-  atb(dz_work, G, h_seq, H, G, H, R, d->L, 1.f, dU);   // dU = sum_r dz_r^T h_{r-1}
-  atb(dz_work, G, nullptr, 0, G, 1, R, 0, 1.f, db);    // db = sum_r dz_r
+  {  // dW, dU, db in one pass over dz, chunks of rows spread over ~4 CTAs per SM
+    const int gx = (G + kWgG - 1) / kWgG, gy = (D + H + 1 + kWgQ - 1) / kWgQ;
+    int64_t split = (int64_t)num_sms() * 4 / (gx * gy);
+    split = split < 1 ? 1 : split;
+    const int64_t tiles = (R + kWgK - 1) / kWgK;
+    if (split > tiles) split = tiles;
+    const int64_t rows_per = (tiles + split - 1) / split * kWgK;
+    const dim3 grid(gx, gy, (unsigned)((R + rows_per - 1) / rows_per));
+    k_lstm_wgrad<<<grid, 256, 0, st>>>(dz_work, x, h_seq, R, d->L, D, H, rows_per, dW, dU, db);
+  }
   if (O > 0) atb(dy, O, h_seq, H, O, H, R, 0, 1.f, dWy);  // dWy = sum_r dy_r^T h_r
   // Hawkes gate: dA, dBm, dC over sequences; d(alpha, beta, mu) per sequence
   atb(dpre_work, H, alpha, MM, H, MM, d->B, 0, 1.f, dA);

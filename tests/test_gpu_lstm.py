@@ -3,7 +3,8 @@ the autograd Function) against the FP64 oracle (oracle/lstm.py): outputs and
 the gradients of every weight, the inputs and the MDHP parameters, for a
 ragged mix of sizes (H not a multiple of 32, per-source and scalar beta,
 single-step sequences, weights staged in shared memory or read from global
-memory)."""
+memory), and each sequences-per-CTA variant of the kernels with a ragged
+last CTA."""
 import numpy as np
 import pytest
 
@@ -14,6 +15,17 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("B,L,D,H,M,nb,O", [(5, 7, 4, 3, 2, 2, 2), (64, 33, 11, 64, 16, 1, 3),
                                              (9, 1, 5, 20, 4, 4, 1), (17, 12, 40, 200, 8, 8, 5)])
 def test_lstm_matches_oracle(B, L, D, H, M, nb, O):
+    _check(B, L, D, H, M, nb, O)
+
+
+@pytest.mark.parametrize("S", [1, 4, 8, 16])
+@pytest.mark.parametrize("B,L,D,H,M,nb,O", [(37, 9, 11, 64, 16, 1, 2), (21, 5, 40, 200, 8, 8, 5)])
+def test_lstm_sequences_per_cta(monkeypatch, S, B, L, D, H, M, nb, O):
+    monkeypatch.setenv("MDHP_LSTM_SEQ_PER_CTA", str(S))
+    _check(B, L, D, H, M, nb, O)
+
+
+def _check(B, L, D, H, M, nb, O):
     from oracle import lstm
 
     import paper_2411_10258_gb300 as mdhp
