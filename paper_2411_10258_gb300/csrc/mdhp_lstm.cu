@@ -414,6 +414,7 @@ __global__ void __launch_bounds__(256) k_lstm_wgrad(const float *dz, const float
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int k = 0; k < 5; ++k) acc[i][k] = 0.f;
+  int m0 = (int)(r0 % L);  // step index of row rb within its sequence
   for (int64_t rb = r0; rb < r1; rb += kWgK) {
     for (int e = tid; e < kWgK * kWgG / 4; e += 256) {
       const int rr = e / (kWgG / 4), c4 = (e % (kWgG / 4)) * 4;
@@ -428,11 +429,17 @@ __global__ void __launch_bounds__(256) k_lstm_wgrad(const float *dz, const float
       float v = 0.f;
       if (rw < r1 && q < Q) {
         if (q < D) v = x[rw * D + q];
-        else if (q < D + H) v = (rw % L) ? hs[(rw - 1) * H + (q - D)] : 0.f;
+        else if (q < D + H) {
+          int m = m0 + rr;
+          while (m >= L) m -= L;
+          v = m ? hs[(rw - 1) * H + (q - D)] : 0.f;
+        }
         else v = 1.f;
       }
       Bs[rr][cc] = v;
     }
+    m0 += kWgK % L;
+    if (m0 >= L) m0 -= L;
     __syncthreads();
 #pragma unroll 8
     for (int k = 0; k < kWgK; ++k) {
@@ -462,11 +469,10 @@ __global__ void __launch_bounds__(256) k_lstm_wgrad(const float *dz, const float
 }
 
 // out[p][q] (+)= scale * sum_{r < R} A(r, p) B(r, q), A(r, p) = A[r * lda + p],
-// B(r, q) = B[r * ldb + q] (or B[(r - 1) * ldb + q] with row r % L == 0 zero
-// when shift_L > 0: h_{t-1}); B == nullptr means B(r, q) = 1 (row sums).
+// B(r, q) = B[r * ldb + q]; B == nullptr means B(r, q) = 1 (row sums).
 // 16 x 16 output tiles, the rows split over gridDim.z slices, atomic adds.
 __global__ void __launch_bounds__(256) k_atb(const float *A, int64_t lda, const float *Bp, int64_t ldb,
-                                             int P, int Q, int64_t R, int shift_L, float scale,
+                                             int P, int Q, int64_t R, float scale,
                                              float *out) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int p = blockIdx.y * 16 + ty, q = blockIdx.x * 16 + tx;
@@ -483,7 +489,6 @@ __global__ void __launch_bounds__(256) k_atb(const float *A, int64_t lda, const 
       float bv = 0.f;
       if (r < r1 && qq < Q) {
         if (!Bp) bv = 1.f;
-        else if (shift_L > 0) bv = (r % shift_L == 0) ? 0.f : Bp[(r - 1) * ldb + qq];
         else bv = Bp[r * ldb + qq];
       }
       Bs[rr][cc] = bv;
@@ -717,10 +722,13 @@ extern "C" mdhp_status mdhp_lstm_backward(
   if (s != MDHP_OK) return s;
   const int64_t R = (int64_t)d->B * d->L;
   auto atb = [&](const float *Ap, int64_t lda, const float *Bp, int64_t ldb, int P, int Q, int64_t rows,
-                 int shift, float scale, float *out) {
-    const int64_t split = rows >= 4096 ? 32 : (rows >= 512 ? 8 : 1);
+                 float scale, float *out) {
+    const int tiles = ((Q + 15) / 16) * ((P + 15) / 16);
+    int64_t split = (int64_t)num_sms() * 8 / tiles;  // about 8 CTAs per SM over the rows
+    const int64_t most = (rows + 31) / 32;
+    split = split < 1 ? 1 : (split > most ? most : split);
     dim3 grid((Q + 15) / 16, (P + 15) / 16, (unsigned)split);
-    k_atb<<<grid, 256, 0, st>>>(Ap, lda, Bp, ldb, P, Q, rows, shift, scale, out);
+    k_atb<<<grid, 256, 0, st>>>(Ap, lda, Bp, ldb, P, Q, rows, scale, out);
   };
   {  // dW, dU, db in one pass over dz, chunks of rows spread over ~4 CTAs per SM
     const int gx = (G + kWgG - 1) / kWgG, gy = (D + H + 1 + kWgQ - 1) / kWgQ;
@@ -732,10 +740,10 @@ extern "C" mdhp_status mdhp_lstm_backward(
     const dim3 grid(gx, gy, (unsigned)((R + rows_per - 1) / rows_per));
     k_lstm_wgrad<<<grid, 256, 0, st>>>(dz_work, x, h_seq, R, d->L, D, H, rows_per, dW, dU, db);
   }
-  if (O > 0) atb(dy, O, h_seq, H, O, H, R, 0, 1.f, dWy);  // dWy = sum_r dy_r^T h_r
+  if (O > 0) atb(dy, O, h_seq, H, O, H, R, 1.f, dWy);  // dWy = sum_r dy_r^T h_r
   // Hawkes gate: dA, dBm, dC over sequences; d(alpha, beta, mu) per sequence
-  atb(dpre_work, H, alpha, MM, H, MM, d->B, 0, 1.f, dA);
-  atb(dpre_work, H, mu, M, H, M, d->B, 0, 1.f, dC);
+  atb(dpre_work, H, alpha, MM, H, MM, d->B, 1.f, dA);
+  atb(dpre_work, H, mu, M, H, M, d->B, 1.f, dC);
   const int eb = 256;
   k_rowmat<<<(int)(((int64_t)d->B * MM + eb - 1) / eb), eb, 0, st>>>(dpre_work, A, d->B, H, MM, 1.f,
                                                                       nullptr, dalpha);
@@ -747,6 +755,6 @@ extern "C" mdhp_status mdhp_lstm_backward(
   // dBm = -sum_b dpre_b^T (beta_b T_b): beta_b T_b formed into the work buffer
   // (free now: the reductions reading dz were enqueued before on this stream)
   k_scale_rows<<<(int)(((int64_t)d->B * nb + eb - 1) / eb), eb, 0, st>>>(beta, T_span, d->B, nb, dz_work);
-  atb(dpre_work, H, dz_work, nb, H, nb, d->B, 0, -1.f, dBm);
+  atb(dpre_work, H, dz_work, nb, H, nb, d->B, -1.f, dBm);
   return launched("lstm hawkes gradients");
 }
