@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(1024) k_lstm_bwd(LstmBwd a) {
 // step t + 1 is fetched during the element-wise phase of step t.  y = Wy h is
 // left to k_lstm_out: it does not feed the recursion.
 template <int S>
-__global__ void __launch_bounds__(1024) k_lstm_fwd_s(LstmFwd a) {
+__global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_fwd_s(LstmFwd a) {
   constexpr int SP = S + 4;
   extern __shared__ __align__(16) float sm[];
   const int H = a.H, D = a.D, G = 4 * H, ZP = G + 1, r = threadIdx.x, nt = blockDim.x;
@@ -211,8 +211,18 @@ __global__ void __launch_bounds__(1024) k_lstm_fwd_s(LstmFwd a) {
   __syncthreads();
   const float br = r < G ? a.b[r] : 0.f;
   const bool tanh_row = r >= 2 * H && r < 3 * H;
+  // The block has at least 4H threads: a thread owns at most S/4 of the S*H
+  // cells, and S/4 register slots cover the S*D inputs when D <= H (wider
+  // inputs fetch the rest after the matvec).
+  constexpr int XI = S / 4, CI = S / 4;
   for (int t = 0; t < a.L; ++t) {
     const float *xc = xs + (t & 1) * D * SP;
+    float xr[XI];  // x_{t+1}, fetched now and stored after the matvec
+#pragma unroll
+    for (int i = 0; i < XI; ++i) {
+      const int p = r + i * nt, s = p / D, q = s0 + s;
+      xr[i] = (t + 1 < a.L && p < S * D && q < a.B) ? a.x[((int64_t)q * a.L + t + 1) * D + p % D] : 0.f;
+    }
     if (r < G) {
       float acc[S];
 #pragma unroll
@@ -248,7 +258,10 @@ __global__ void __launch_bounds__(1024) k_lstm_fwd_s(LstmFwd a) {
       }
     }
     __syncthreads();
-    for (int p = r; p < S * H; p += nt) {
+#pragma unroll
+    for (int i = 0; i < CI; ++i) {
+      const int p = r + i * nt;
+      if (p >= S * H) break;
       const int s = p / H, j = p % H, q = s0 + s;
       const float *zs = z + s * ZP;
       const float cn = kh[p] * fmaf(zs[H + j], c[p], zs[j] * zs[2 * H + j]);
@@ -261,12 +274,15 @@ __global__ void __launch_bounds__(1024) k_lstm_fwd_s(LstmFwd a) {
         a.hs[o] = hn;
       }
     }
-    if (t + 1 < a.L) {
-      float *xn = xs + ((t + 1) & 1) * D * SP;
-      for (int p = r; p < S * D; p += nt) {
-        const int s = p / D, d = p % D, q = s0 + s;
-        xn[d * SP + s] = q < a.B ? a.x[((int64_t)q * a.L + t + 1) * D + d] : 0.f;
-      }
+    float *xn = xs + ((t + 1) & 1) * D * SP;
+#pragma unroll
+    for (int i = 0; i < XI; ++i) {
+      const int p = r + i * nt;
+      if (p < S * D) xn[(p % D) * SP + p / D] = xr[i];
+    }
+    for (int p = r + XI * nt; p < S * D; p += nt) {
+      const int q = s0 + p / D;
+      xn[(p % D) * SP + p / D] = (t + 1 < a.L && q < a.B) ? a.x[((int64_t)q * a.L + t + 1) * D + p % D] : 0.f;
     }
     __syncthreads();
   }
@@ -298,7 +314,7 @@ __global__ void k_lstm_out(const float *hs, const float *Wy, int64_t R, int H, i
 // with thread (u, group) owning GW sequences of output unit u: one weight
 // load and GW/4 16-byte loads of dzT feed GW FMAs.
 template <int S>
-__global__ void __launch_bounds__(1024) k_lstm_bwd_s(LstmBwd a) {
+__global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_bwd_s(LstmBwd a) {
   constexpr int SP = S + 4, GW = S >= 16 ? 8 : 4;
   extern __shared__ __align__(16) float sm[];
   const int H = a.H, D = a.D, G = 4 * H, HD = H + D, r = threadIdx.x, nt = blockDim.x;
@@ -323,8 +339,34 @@ __global__ void __launch_bounds__(1024) k_lstm_bwd_s(LstmBwd a) {
   }
   __syncthreads();
   const int items = HD * (S / GW);
+  // The block has at least 4H threads: a thread owns at most S/4 of the S*H
+  // cells.  Their saved gates, cell states and first output gradient for the
+  // next step down are fetched into registers before the matvec phase.
+  constexpr int CI = S / 4;
+  float pf[CI][7];
+  auto fetch = [&](int t) {
+#pragma unroll
+    for (int i = 0; i < CI; ++i) {
+      const int p = r + i * nt, s = p / H, j = p % H, q = s0 + s;
+      if (p < S * H && q < a.B) {
+        const int64_t row = (int64_t)q * a.L + t;
+        const float *gr = a.gates + row * G;
+        pf[i][0] = gr[j];
+        pf[i][1] = gr[H + j];
+        pf[i][2] = gr[2 * H + j];
+        pf[i][3] = gr[3 * H + j];
+        pf[i][4] = a.cs[row * H + j];
+        pf[i][5] = t > 0 ? a.cs[(row - 1) * H + j] : 0.f;
+        pf[i][6] = a.O > 0 ? a.dy[row * a.O] : 0.f;
+      }
+    }
+  };
+  fetch(a.L - 1);
   for (int t = a.L - 1; t >= 0; --t) {
-    for (int p = r; p < S * H; p += nt) {
+#pragma unroll
+    for (int i = 0; i < CI; ++i) {
+      const int p = r + i * nt;
+      if (p >= S * H) break;
       const int s = p / H, j = p % H, q = s0 + s;
       if (q >= a.B) {
         dzT[j * SP + s] = dzT[(H + j) * SP + s] = dzT[(2 * H + j) * SP + s] = dzT[(3 * H + j) * SP + s] = 0.f;
@@ -332,11 +374,10 @@ __global__ void __launch_bounds__(1024) k_lstm_bwd_s(LstmBwd a) {
       }
       const int64_t row = (int64_t)q * a.L + t;
       float dht = dh[p];
-      for (int k = 0; k < a.O; ++k) dht = fmaf(a.Wy[(int64_t)k * H + j], a.dy[row * a.O + k], dht);
-      const float *gr = a.gates + row * G;
-      const float ig = gr[j], fg = gr[H + j], gg = gr[2 * H + j], og = gr[3 * H + j];
-      const float cv = a.cs[row * H + j];
-      const float cp = t > 0 ? a.cs[(row - 1) * H + j] : 0.f;
+      if (a.O > 0) dht = fmaf(a.Wy[j], pf[i][6], dht);
+      for (int k = 1; k < a.O; ++k) dht = fmaf(a.Wy[(int64_t)k * H + j], a.dy[row * a.O + k], dht);
+      const float ig = pf[i][0], fg = pf[i][1], gg = pf[i][2], og = pf[i][3];
+      const float cv = pf[i][4], cp = pf[i][5];
       const float tc = tanhf(cv);
       const float dc = fmaf(dht * og, 1.f - tc * tc, dcn[p]);
       dhk[p] = fmaf(dc, fmaf(fg, cp, ig * gg), dhk[p]);
@@ -357,6 +398,7 @@ __global__ void __launch_bounds__(1024) k_lstm_bwd_s(LstmBwd a) {
       dcn[p] = din * fg;
     }
     __syncthreads();
+    if (t > 0) fetch(t - 1);
     for (int it = r; it < items; it += nt) {
       const int u = it % HD, sb = (it / HD) * GW;
       float acc[GW];
@@ -565,17 +607,16 @@ int resident(K kernel, int threads, int smem) {
 // eight sequences' arithmetic plus a part linear in S; on GB300 at H = 64,
 // D = 11 the measured fwd+bwd times for S = 1, 4, 8, 16 over 4,096
 // sequences were 15.9, 11.2, 10.8 and 10.8 ms.  Both passes use the same S;
-// the forward kernel's residency decides.  MDHP_LSTM_SEQ_PER_CTA overrides
-// the choice.
+// the forward kernel's residency decides.  MDHP_LSTM_SEQ_PER_CTA (1, 4, 8,
+// 16) overrides the choice where that S can run.
 int pick_seq_per_cta(int B, int D, int H) {
-  if (const char *e = getenv("MDHP_LSTM_SEQ_PER_CTA")) {
-    const int v = atoi(e);
-    if (v == 1 || v == 4 || v == 8 || v == 16) return v;
-  }
   const int G = 4 * H, threads = (G + 31) / 32 * 32, lim = max_smem();
+  int forced = 0;
+  if (const char *e = getenv("MDHP_LSTM_SEQ_PER_CTA")) forced = atoi(e);
   int best = 1;
   double best_cost = 1e300;
   for (int S : {1, 4, 8, 16}) {
+    if (S == 16 && threads > 512) continue;  // its register budget assumes <= 512 threads
     int smem = fwd_smem(S, D, H, true);
     if (smem > lim) smem = fwd_smem(S, D, H, false);
     if (smem > lim) continue;
@@ -587,6 +628,7 @@ int pick_seq_per_cta(int B, int D, int H) {
       default: res = resident(k_lstm_fwd_s<16>, threads, smem); break;
     }
     if (res < 1) continue;
+    if (S == forced) return S;
     const int64_t blocks = ((int64_t)B + S - 1) / S, slots = (int64_t)res * num_sms();
     const double cost = (double)((blocks + slots - 1) / slots) * (S + 8);
     if (cost <= best_cost) {
