@@ -256,8 +256,7 @@ struct XAcc {
     sm.P[(threadIdx.x + i) * PP + M] = gm;
   }
   // the event at sorted position p with features x
-  __device__ __forceinline__ void event(int p, const float4 (&x)[NQ], const Sm<M> &sm, float &Ls,
-                                        float &Lc) {
+  __device__ __forceinline__ float event(int p, const float4 (&x)[NQ], const Sm<M> &sm) {
     while (p >= te) {  // leave type i (types with no events are passed over)
       flush(sm);
 #pragma unroll
@@ -269,17 +268,17 @@ struct XAcc {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) ar[q] = reinterpret_cast<const float4 *>(sm.alpha + i * AP)[q];
     }
-    float d0 = mu, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+    float d0 = mu, d1 = 0.f;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       d0 = fmaf(ar[q].x, x[q].x, d0);
       d1 = fmaf(ar[q].y, x[q].y, d1);
-      d2 = fmaf(ar[q].z, x[q].z, d2);
-      d3 = fmaf(ar[q].w, x[q].w, d3);
+      d0 = fmaf(ar[q].z, x[q].z, d0);
+      d1 = fmaf(ar[q].w, x[q].w, d1);
     }
-    const float lam = (d0 + d1) + (d2 + d3);
-    const float r = __fdividef(1.f, lam);
-    kahan_add(Ls, Lc, __log2f(lam));
+    const float lam = d0 + d1;
+    const float r = rcp_ftz(lam);
+    const float lg = lg2_ftz(lam);
     gm += r;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -288,6 +287,7 @@ struct XAcc {
       g[q].z = fmaf(r, x[q].z, g[q].z);
       g[q].w = fmaf(r, x[q].w, g[q].w);
     }
+    return lg;
   }
 };
 
@@ -296,6 +296,7 @@ struct XAcc {
 // memory one step ahead in registers).  Two events per trip with two
 // register buffers (no copies between them); with the block size a
 // compile-time constant (NTC > 0) every global load is base + constant.
+// The two events' log-intensities are added before the compensated sum.
 template <int M, bool XS, int NTC, typename XP>
 __device__ __forceinline__ void xpass(int p0, int p1, int i0, XP X, int xcap, XMap m,
                                       const Sm<M> &sm, float &Ls, float &Lc) {
@@ -319,14 +320,17 @@ __device__ __forceinline__ void xpass(int p0, int p1, int i0, XP X, int xcap, XM
 #pragma unroll
       for (int q = 0; q < NQ; ++q) xb[q] = px[ps + q * qs];
     }
-    acc.event(p, xa, sm, Ls, Lc);
-    if (!hb) break;
+    const float la = acc.event(p, xa, sm);
+    if (!hb) {
+      kahan_add(Ls, Lc, la);
+      break;
+    }
     const bool ha = p + 2 < p1;
     if (ha) {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) xa[q] = px[2 * ps + q * qs];
     }
-    acc.event(p + 1, xb, sm, Ls, Lc);
+    kahan_add(Ls, Lc, la + acc.event(p + 1, xb, sm));
     if (!ha) break;
     p += 2;
     px += 2 * ps;
@@ -374,6 +378,7 @@ __device__ __forceinline__ bool xpass_pipe(int p0, int p1, int i0, XPipe &pp, co
   const bool active = p0 < p1;
   XAcc<M> acc;
   if (active) acc.begin(i0, sm);
+  float pend = 0.f;  // log2 of the first event of a pair, summed as in xpass
   for (int s = 0; s < pp.nst; ++s) {
     const uint32_t g = pp.used;
     const int slot = (int)(g % (uint32_t)pp.D);
@@ -387,7 +392,9 @@ __device__ __forceinline__ bool xpass_pipe(int p0, int p1, int i0, XPipe &pp, co
         float4 x[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) x[q] = buf[(k - k0) * pp.step_f4 + q * NT];
-        acc.event(p, x, sm, Ls, Lc);
+        const float lg = acc.event(p, x, sm);
+        if ((k & 1) == 0) pend = lg;
+        else kahan_add(Ls, Lc, pend + lg);
       }
     }
     __syncthreads();
@@ -395,7 +402,10 @@ __device__ __forceinline__ bool xpass_pipe(int p0, int p1, int i0, XPipe &pp, co
     if (sm.ctl[3]) return false;
     if (tid == 0) xpipe_issue<M>(pp, sm);
   }
-  if (active) acc.flush(sm);
+  if (active) {
+    if ((p1 - p0) & 1) kahan_add(Ls, Lc, pend);  // the unpaired last event
+    acc.flush(sm);
+  }
   return true;
 }
 

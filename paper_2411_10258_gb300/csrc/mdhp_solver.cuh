@@ -76,6 +76,22 @@ __device__ __forceinline__ float exp2_acc(float x) {
   return x < -125.f ? 0.f : r;
 }
 
+// Hardware base-2 logarithm and reciprocal of an intensity (PTX lg2.approx /
+// rcp.approx, flush-to-zero forms: no subnormal scaling).  An intensity is at
+// least mu_floor (default 1e-10), far above the subnormal range; one below
+// 2^-126 reads as 0, its log as -inf, and the evaluation is reported
+// non-finite.
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   const float y = x - c;
   const float t = s + y;
@@ -502,9 +518,9 @@ __device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float 
 #pragma unroll
     for (int o = 1; o < SPL; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
     const float lam = sm.mu[un] + dot;
-    const float r = __fdividef(1.f, lam);
+    const float r = rcp_ftz(lam);
     if (s == 0) {
-      kahan_add(Ls, Lc, __log2f(lam));
+      kahan_add(Ls, Lc, lg2_ftz(lam));
       if (PRIV) sm.mpriv[un * (NT / SPL) + c] += r;
       else atomicAdd(&sm.gm[un], r);
       if (r_out) r_out[n] = r;
@@ -727,9 +743,9 @@ __device__ __forceinline__ void pass2_fixed(int c, int s, int b0, int b1, const 
 #pragma unroll
     for (int o = 1; o < SPL; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
     const float lam = sm.mu[un] + dot;
-    const float r = __fdividef(1.f, lam);
+    const float r = rcp_ftz(lam);
     if (s == 0) {
-      kahan_add(Ls, Lc, __log2f(lam));
+      kahan_add(Ls, Lc, lg2_ftz(lam));
       if (PRIV) sm.mpriv[un * (NT / SPL) + c] += r;
       else atomicAdd(&sm.gm[un], r);
       if (r_out) r_out[n] = r;
