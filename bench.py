@@ -30,7 +30,7 @@ METRIC = "MDHP window fits/s to fixed logL tol (warm vs cold); LL+grad events/s 
 # DRAM read + write of one fit of the default workload (4,096 windows x M=16,
 # 200 iterations), from an ncu app-range capture of one --profile-step fit
 # (summary under profiles/); to be re-taken whenever the fit kernels change
-FIT_DRAM_BYTES_4096xM16 = 75324928 + 39829760
+FIT_DRAM_BYTES_4096xM16 = 75271168 + 39822080
 UNIT = "windows/s"
 WORKLOAD = "4096 windows x M=16, counts log-uniform[200,5000], scalar beta=1 fixed, 200 PGD iterations (lr 1e-2), cold start"
 
