@@ -18,6 +18,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -50,6 +51,8 @@ def parse():
                     help="2: fixed-iteration fits (default line); 5: warm vs cold fits to tolerance")
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="folder for the raw nvidia-smi clock samples (default: the temp folder)")
     ap.add_argument("--attack-windows", type=int, default=128,
                     help="attacked (and as many normal) windows per combination (--workload attack)")
     ap.add_argument("--profile-step", action="store_true",
@@ -77,10 +80,10 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, directory: str | None = None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"mdhp_clocks_gpu{gpu_index}.csv")
 
     def __enter__(self):
         try:
@@ -279,7 +282,7 @@ def run_ours(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     kern_ms = []
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clocks_dir)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -435,7 +438,7 @@ def run_long_learned(args):
     torch.cuda.synchronize()
     plan.set_timing(True)
     ms = []
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(0, args.clocks_dir)
     with sampler:
         for _ in range(args.steps):
             out = plan.fit(db, opts, mu, al, be.copy_(beta0))
@@ -592,11 +595,13 @@ def run_lstm(args):
         step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        step()
-    e1.record()
-    torch.cuda.synchronize()
+    sampler = ClockSampler(0, args.clocks_dir)
+    with sampler:
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     G = 4 * H
     fwd = 2 * G * (D + H) + 10 * H + 2 * O * H           # per step and sequence
@@ -613,7 +618,8 @@ def run_lstm(args):
             "config": {"workload": f"{B} windows x {L} messages x {D} inputs, H={H}, M={M}, scalar beta, O={O}"},
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                          "flops_per_step_sequence": fwd + bwd, "traffic": None,
-                         "kernel": "k_lstm_fwd_s / k_lstm_bwd_s (S sequences per CTA through time)"}}
+                         "kernel": "k_lstm_fwd_s / k_lstm_bwd_s (S sequences per CTA through time)"},
+            "clocks": sampler.summary()}
     print(json.dumps(line), flush=True)
 
 
