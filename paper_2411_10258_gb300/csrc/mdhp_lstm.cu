@@ -26,6 +26,14 @@ namespace {
 
 __device__ __forceinline__ float sigm(float z) { return 1.f / (1.f + expf(-z)); }
 
+// Gate activations of the multi-sequence kernels from the fast exponential
+// and division intrinsics: sigmoid(z) = 1 / (1 + e^-z), tanh(z) =
+// 2 sigmoid(2z) - 1.  Error about 1e-6 relative for the sigmoid and 1e-7
+// absolute for tanh (the intrinsic's error grows with |z|, and at |z| > 80
+// e^-z overflows to inf, where the quotient is 0).
+__device__ __forceinline__ float sigm_fast(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
+__device__ __forceinline__ float tanh_fast(float z) { return fmaf(2.f, sigm_fast(2.f * z), -1.f); }
+
 struct LstmFwd {
   int B, L, D, H, M, nb, O, staged;
   const float *x, *mu, *alpha, *beta, *T, *W, *U, *b, *A, *Bm, *C, *Wy;
@@ -170,8 +178,9 @@ __global__ void __launch_bounds__(1024) k_lstm_bwd(LstmBwd a) {
 // unit index fastest and its global loads and stores coalesce.  The input of
 // step t + 1 is fetched during the element-wise phase of step t.  y = Wy h is
 // left to k_lstm_out: it does not feed the recursion.
-template <int S>
+template <int S, bool ST>
 __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_fwd_s(LstmFwd a) {
+  constexpr bool STG = ST;
   constexpr int SP = S + 4;
   extern __shared__ __align__(16) float sm[];
   const int H = a.H, D = a.D, G = 4 * H, ZP = G + 1, r = threadIdx.x, nt = blockDim.x;
@@ -183,7 +192,7 @@ __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_fwd_s(LstmFwd a) 
   float *z = kh + S * H;        // [S][ZP]     gate activations of step t
   float *WT = z + S * ZP;       // [D][G]      (staged)
   float *UT = WT + D * G;       // [H][G]
-  if (a.staged) {
+  if (STG) {
     for (int p = r; p < G * D; p += nt) WT[(p % D) * G + p / D] = a.W[p];
     for (int p = r; p < G * H; p += nt) UT[(p % H) * G + p / H] = a.U[p];
   }
@@ -228,7 +237,7 @@ __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_fwd_s(LstmFwd a) 
 #pragma unroll
       for (int e = 0; e < S; ++e) acc[e] = br;
       for (int d = 0; d < D; ++d) {
-        const float w = a.staged ? WT[d * G + r] : a.W[(int64_t)r * D + d];
+        const float w = STG ? WT[d * G + r] : a.W[(int64_t)r * D + d];
 #pragma unroll
         for (int e = 0; e < S; e += 4) {
           const float4 v = *reinterpret_cast<const float4 *>(xc + d * SP + e);
@@ -240,7 +249,7 @@ __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_fwd_s(LstmFwd a) 
       }
 #pragma unroll 4
       for (int k = 0; k < H; ++k) {
-        const float w = a.staged ? UT[k * G + r] : a.U[(int64_t)r * H + k];
+        const float w = STG ? UT[k * G + r] : a.U[(int64_t)r * H + k];
 #pragma unroll
         for (int e = 0; e < S; e += 4) {
           const float4 v = *reinterpret_cast<const float4 *>(h + k * SP + e);
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_fwd_s(LstmFwd a) 
       }
 #pragma unroll
       for (int e = 0; e < S; ++e) {
-        const float v = tanh_row ? tanhf(acc[e]) : sigm(acc[e]);
+        const float v = tanh_row ? tanh_fast(acc[e]) : sigm_fast(acc[e]);
         z[e * ZP + r] = v;
         if (s0 + e < a.B) a.gates[((int64_t)(s0 + e) * a.L + t) * G + r] = v;
       }
@@ -265,7 +274,7 @@ __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_fwd_s(LstmFwd a) 
       const int s = p / H, j = p % H, q = s0 + s;
       const float *zs = z + s * ZP;
       const float cn = kh[p] * fmaf(zs[H + j], c[p], zs[j] * zs[2 * H + j]);
-      const float hn = zs[3 * H + j] * tanhf(cn);
+      const float hn = zs[3 * H + j] * tanh_fast(cn);
       c[p] = cn;
       h[j * SP + s] = hn;
       if (q < a.B) {
@@ -313,8 +322,9 @@ __global__ void k_lstm_out(const float *hs, const float *Wy, int64_t R, int H, i
 // to dzT [G][SP].  The matvec phase computes [dh_{t-1}; dx_t] = [U | W]^T dz
 // with thread (u, group) owning GW sequences of output unit u: one weight
 // load and GW/4 16-byte loads of dzT feed GW FMAs.
-template <int S>
+template <int S, bool ST>
 __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_bwd_s(LstmBwd a) {
+  constexpr bool STG = ST;
   constexpr int SP = S + 4, GW = S >= 16 ? 8 : 4;
   extern __shared__ __align__(16) float sm[];
   const int H = a.H, D = a.D, G = 4 * H, HD = H + D, r = threadIdx.x, nt = blockDim.x;
@@ -325,7 +335,7 @@ __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_bwd_s(LstmBwd a) 
   float *dhk = dcn + S * H;      // [S][H]  d hks accumulated over steps
   float *kh = dhk + S * H;       // [S][H]
   float *V = kh + S * H;         // [G][HD] rows of [U | W] (staged)
-  if (a.staged)
+  if (STG)
     for (int p = r; p < G * HD; p += nt) {
       const int g = p / HD, u = p % HD;
       V[p] = u < H ? a.U[(int64_t)g * H + u] : a.W[(int64_t)g * D + (u - H)];
@@ -378,7 +388,7 @@ __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_bwd_s(LstmBwd a) 
       for (int k = 1; k < a.O; ++k) dht = fmaf(a.Wy[(int64_t)k * H + j], a.dy[row * a.O + k], dht);
       const float ig = pf[i][0], fg = pf[i][1], gg = pf[i][2], og = pf[i][3];
       const float cv = pf[i][4], cp = pf[i][5];
-      const float tc = tanhf(cv);
+      const float tc = tanh_fast(cv);
       const float dc = fmaf(dht * og, 1.f - tc * tc, dcn[p]);
       dhk[p] = fmaf(dc, fmaf(fg, cp, ig * gg), dhk[p]);
       const float din = dc * kh[p];
@@ -406,7 +416,7 @@ __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_bwd_s(LstmBwd a) 
       for (int e = 0; e < GW; ++e) acc[e] = 0.f;
 #pragma unroll 4
       for (int g = 0; g < G; ++g) {
-        const float w = a.staged ? V[g * HD + u]
+        const float w = STG ? V[g * HD + u]
                                  : (u < H ? a.U[(int64_t)g * H + u] : a.W[(int64_t)g * D + (u - H)]);
 #pragma unroll
         for (int e = 0; e < GW; e += 4) {
@@ -440,8 +450,14 @@ __global__ void __launch_bounds__(S >= 16 ? 512 : 1024) k_lstm_bwd_s(LstmBwd a) 
 // i.e. out[g][q] = sum_r dz[r][g] Bc[r][q] with Bc[r] = [x_r, h_{r-1}, 1]
 // (h_{r-1} = 0 at the first step of a sequence).  A CTA owns a 64 x 80 tile
 // of (g, q) over a chunk of rows, staged 32 rows at a time; thread (tg, tq)
-// keeps a 4 x 5 register tile.  Chunks meet in the output by atomic adds.
+// keeps a 4 x 5 register tile.  The next 32 rows are fetched into registers
+// while the current ones are multiplied.  Chunks meet in the output by
+// atomic adds.
 constexpr int kWgG = 64, kWgQ = 80, kWgK = 32;
+constexpr int kWgA = kWgK * kWgG / 4 / 256;  // float4 of dz per thread per stage
+constexpr int kWgB = kWgK * kWgQ / 256;      // elements of Bc per thread per stage
+static_assert(kWgK * kWgG / 4 == kWgA * 256 && kWgK * kWgQ == kWgB * 256, "stage split");
+
 __global__ void __launch_bounds__(256) k_lstm_wgrad(const float *dz, const float *x, const float *hs,
                                                     int64_t R, int L, int D, int H, int64_t rows_per,
                                                     float *dW, float *dU, float *db) {
@@ -451,38 +467,63 @@ __global__ void __launch_bounds__(256) k_lstm_wgrad(const float *dz, const float
   const int tg = tid & 15, tq = tid >> 4;
   const int g0 = blockIdx.x * kWgG, q0 = blockIdx.y * kWgQ;
   const int64_t r0 = blockIdx.z * rows_per, r1 = r0 + rows_per < R ? r0 + rows_per : R;
+  float4 an[kWgA];
+  float bn[kWgB];
+  // rows rb .. rb + 31 into registers; m0 = step index of row rb in its sequence
+  auto fetch = [&](int64_t rb, int m0) {
+#pragma unroll
+    for (int j = 0; j < kWgA; ++j) {
+      const int e = tid + j * 256, rr = e / (kWgG / 4), c4 = (e % (kWgG / 4)) * 4;
+      const int64_t rw = rb + rr;
+      an[j] = (rw < r1 && g0 + c4 < G) ? *reinterpret_cast<const float4 *>(dz + rw * G + g0 + c4)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < kWgB; ++j) {
+      const int e = tid + j * 256, rr = e / kWgQ, q = q0 + e % kWgQ;
+      const int64_t rw = rb + rr;
+      float v = 0.f;
+      if (rw < r1 && q < Q) {
+        if (q < D) {
+          v = x[rw * D + q];
+        } else if (q < D + H) {
+          int m = m0 + rr;
+          while (m >= L) m -= L;
+          v = m ? hs[(rw - 1) * H + (q - D)] : 0.f;
+        } else {
+          v = 1.f;
+        }
+      }
+      bn[j] = v;
+    }
+  };
+  auto stage = [&]() {
+#pragma unroll
+    for (int j = 0; j < kWgA; ++j) {
+      const int e = tid + j * 256;
+      *reinterpret_cast<float4 *>(&As[e / (kWgG / 4)][(e % (kWgG / 4)) * 4]) = an[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kWgB; ++j) {
+      const int e = tid + j * 256;
+      Bs[e / kWgQ][e % kWgQ] = bn[j];
+    }
+  };
   float acc[4][5];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int k = 0; k < 5; ++k) acc[i][k] = 0.f;
-  int m0 = (int)(r0 % L);  // step index of row rb within its sequence
+  int m0 = (int)(r0 % L);
+  const int mstep = kWgK % L;
+  fetch(r0, m0);
+  stage();
+  __syncthreads();
   for (int64_t rb = r0; rb < r1; rb += kWgK) {
-    for (int e = tid; e < kWgK * kWgG / 4; e += 256) {
-      const int rr = e / (kWgG / 4), c4 = (e % (kWgG / 4)) * 4;
-      const int64_t rw = rb + rr;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (rw < r1 && g0 + c4 < G) v = *reinterpret_cast<const float4 *>(dz + rw * G + g0 + c4);
-      *reinterpret_cast<float4 *>(&As[rr][c4]) = v;
-    }
-    for (int e = tid; e < kWgK * kWgQ; e += 256) {
-      const int rr = e / kWgQ, cc = e % kWgQ, q = q0 + cc;
-      const int64_t rw = rb + rr;
-      float v = 0.f;
-      if (rw < r1 && q < Q) {
-        if (q < D) v = x[rw * D + q];
-        else if (q < D + H) {
-          int m = m0 + rr;
-          while (m >= L) m -= L;
-          v = m ? hs[(rw - 1) * H + (q - D)] : 0.f;
-        }
-        else v = 1.f;
-      }
-      Bs[rr][cc] = v;
-    }
-    m0 += kWgK % L;
+    const bool more = rb + kWgK < r1;
+    m0 += mstep;
     if (m0 >= L) m0 -= L;
-    __syncthreads();
+    if (more) fetch(rb + kWgK, m0);
 #pragma unroll 8
     for (int k = 0; k < kWgK; ++k) {
       const float4 av = *reinterpret_cast<const float4 *>(&As[k][tg * 4]);
@@ -494,6 +535,8 @@ __global__ void __launch_bounds__(256) k_lstm_wgrad(const float *dz, const float
         for (int i = 0; i < 4; ++i) acc[i][c] = fmaf(a4[i], bv, acc[i][c]);
       }
     }
+    __syncthreads();
+    if (more) stage();
     __syncthreads();
   }
 #pragma unroll
@@ -617,15 +660,18 @@ int pick_seq_per_cta(int B, int D, int H) {
   double best_cost = 1e300;
   for (int S : {1, 4, 8, 16}) {
     if (S == 16 && threads > 512) continue;  // its register budget assumes <= 512 threads
-    int smem = fwd_smem(S, D, H, true);
-    if (smem > lim) smem = fwd_smem(S, D, H, false);
+    const bool stg = fwd_smem(S, D, H, true) <= lim;
+    const int smem = fwd_smem(S, D, H, stg);
     if (smem > lim) continue;
     int res = 0;
     switch (S) {
       case 1: res = resident(k_lstm_fwd, threads, smem); break;
-      case 4: res = resident(k_lstm_fwd_s<4>, threads, smem); break;
-      case 8: res = resident(k_lstm_fwd_s<8>, threads, smem); break;
-      default: res = resident(k_lstm_fwd_s<16>, threads, smem); break;
+      case 4: res = stg ? resident(k_lstm_fwd_s<4, true>, threads, smem)
+                        : resident(k_lstm_fwd_s<4, false>, threads, smem); break;
+      case 8: res = stg ? resident(k_lstm_fwd_s<8, true>, threads, smem)
+                        : resident(k_lstm_fwd_s<8, false>, threads, smem); break;
+      default: res = stg ? resident(k_lstm_fwd_s<16, true>, threads, smem)
+                         : resident(k_lstm_fwd_s<16, false>, threads, smem); break;
     }
     if (res < 1) continue;
     if (S == forced) return S;
@@ -644,8 +690,9 @@ void launch_fwd(const LstmFwd &a0, int threads, cudaStream_t st) {
   LstmFwd a = a0;
   a.staged = fwd_smem(S, a.D, a.H, true) <= max_smem() ? 1 : 0;
   const int smem = fwd_smem(S, a.D, a.H, a.staged);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_lstm_fwd_s<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_lstm_fwd_s<S><<<(a.B + S - 1) / S, threads, smem, st>>>(a);
+  auto k = a.staged ? k_lstm_fwd_s<S, true> : k_lstm_fwd_s<S, false>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k<<<(a.B + S - 1) / S, threads, smem, st>>>(a);
 }
 
 template <int S>
@@ -653,8 +700,9 @@ void launch_bwd(const LstmBwd &a0, int threads, cudaStream_t st) {
   LstmBwd a = a0;
   a.staged = bwd_smem(S, a.D, a.H, true) <= max_smem() ? 1 : 0;
   const int smem = bwd_smem(S, a.D, a.H, a.staged);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_lstm_bwd_s<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_lstm_bwd_s<S><<<(a.B + S - 1) / S, threads, smem, st>>>(a);
+  auto k = a.staged ? k_lstm_bwd_s<S, true> : k_lstm_bwd_s<S, false>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k<<<(a.B + S - 1) / S, threads, smem, st>>>(a);
 }
 
 mdhp_status check_dims(const mdhp_lstm_dims *d) {
@@ -772,9 +820,12 @@ extern "C" mdhp_status mdhp_lstm_backward(
     dim3 grid((Q + 15) / 16, (P + 15) / 16, (unsigned)split);
     k_atb<<<grid, 256, 0, st>>>(Ap, lda, Bp, ldb, P, Q, rows, scale, out);
   };
-  {  // dW, dU, db in one pass over dz, chunks of rows spread over ~4 CTAs per SM
+  {  // dW, dU, db in one pass over dz, chunks of rows filling one wave of CTAs
     const int gx = (G + kWgG - 1) / kWgG, gy = (D + H + 1 + kWgQ - 1) / kWgQ;
-    int64_t split = (int64_t)num_sms() * 4 / (gx * gy);
+    int res = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, k_lstm_wgrad, 256, 0) != cudaSuccess || res < 1)
+      res = 1;
+    int64_t split = (int64_t)num_sms() * res / (gx * gy);
     split = split < 1 ? 1 : split;
     const int64_t tiles = (R + kWgK - 1) / kWgK;
     if (split > tiles) split = tiles;
