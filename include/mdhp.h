@@ -215,7 +215,7 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
  * plan.  Candidates: 64, 128 and 256 threads per window; for the decoupled
  * fixed-beta kernels the shared-memory class (none, half, the largest that
  * fits), the feature ring (none; 1x4, 2x3, 2x4, 4x3 steps x stages) and the
- * two-launch split (off; 256 x 1, 128 x 1, 128 x 2 long threads x CTAs per
+ * two-launch split (off; 256 x 1, 256 x 2, 128 x 1, 128 x 2 long threads x CTAs per
  * SM); for the event recursion every built threads-per-chunk split and the
  * staging cutoff (none, the default, the largest that fits).  Each candidate
  * runs tune_iters iterations (<= 0: 20) with tol = 0 after one warm-up run.

@@ -1011,7 +1011,7 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
         if (fit >= 64) cands.push_back({nt, 0, fit, pd[0], pd[1], 0, 256, 1});
       }
       if (fit >= 128) cands.push_back({nt, 0, fit / 2 / 32 * 32, 0, 0, 0, 256, 1});
-      static const int kSplits[][2] = {{256, 1}, {128, 1}, {128, 2}};
+      static const int kSplits[][2] = {{256, 1}, {256, 2}, {128, 1}, {128, 2}};
       for (const auto &sp : kSplits)
         if (sp[0] != nt && nt < 256) cands.push_back({nt, 0, 0, 0, 0, 1, sp[0], sp[1]});
     } else {
