@@ -19,8 +19,11 @@ def test_lstm_matches_oracle(B, L, D, H, M, nb, O):
 
 
 @pytest.mark.parametrize("S", [1, 4, 8, 16])
-@pytest.mark.parametrize("B,L,D,H,M,nb,O", [(37, 9, 11, 64, 16, 1, 2), (21, 5, 40, 200, 8, 8, 5)])
+@pytest.mark.parametrize("B,L,D,H,M,nb,O", [(37, 9, 11, 64, 16, 1, 2), (21, 5, 40, 200, 8, 8, 5),
+                                             (13, 6, 30, 12, 4, 4, 2)])
 def test_lstm_sequences_per_cta(monkeypatch, S, B, L, D, H, M, nb, O):
+    # (13, 6, 30, 12): inputs wider than the hidden state, so part of each
+    # step's inputs is fetched after the matvec rather than ahead of it
     monkeypatch.setenv("MDHP_LSTM_SEQ_PER_CTA", str(S))
     _check(B, L, D, H, M, nb, O)
 
