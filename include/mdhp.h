@@ -451,6 +451,12 @@ mdhp_status mdhp_simulate(int32_t M, int32_t beta_mode, int32_t B, const double 
  * MDHP inputs (mu, alpha, beta); dW, dU, db, dA, dBm, dC, dWy are
  * overwritten; dz_work [B][L][4H] and dpre_work [B][H] are scratch.
  * Limits: H 1..256, D <= 3H, O <= 4H, M 1..64, L >= 1; MDHP_E_ARG otherwise.
+ * Both calls are asynchronous on `stream` and allocate nothing.  Execution:
+ * one CTA carries S in {1, 4, 8, 16} sequences through all L steps, S chosen
+ * from the batch size and the kernels' occupancy (environment variable
+ * MDHP_LSTM_SEQ_PER_CTA = 1, 4, 8 or 16 forces a value that can run).  For
+ * S > 1 the gate activations use the fast exponential and division
+ * (about 1e-6 relative for the sigmoid, 1e-7 absolute for tanh).
  */
 typedef struct {
   int32_t B, L, D, H, M, nb, O;
