@@ -1,7 +1,8 @@
 """bench.py's reference arm (the FP64 oracle on the host cores) prints one
 JSON line with the keys the benchmark contract asks for: the same metric and
 unit as the GPU arm, impl = reference, a cpu_baseline describing the run and
-an e2e block with no host/device copies.  Runs a one-step sample on the CPU."""
+an e2e block with no host/device copies; under torchrun only rank 0 prints.
+Runs a one-step sample on the CPU."""
 import json
 import os
 import subprocess
@@ -27,3 +28,11 @@ def test_reference_arm_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert "workload" in d["config"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
