@@ -3,12 +3,14 @@
 Plain numpy restatement of what include/mdhp.h documents for the
 initializer: the per-window features (type shares, 32-bin log-gap histograms
 per ordered type pair, log N, log T, beta), the 4-layer ReLU MLP, the head and
-the training loss with its gradient, and one AdamW step.  ``bf16=True``
-rounds inputs, weights and hidden activations to bfloat16 at the same points
-as the GPU path (round to nearest even), so the comparison measures only the
-accumulation order; ``bf16=False`` gives the exact FP64 function, which the
-CPU tests pin by central finite differences.  Shares no code with the CUDA
-path.
+the training loss with its gradient, and one AdamW step.  The reference is the
+exact FP64 function (``bf16=False``): the CPU tests pin it by central finite
+differences and closed forms, and the GPU tests compare the BF16 kernels with
+it at tolerances derived from BF16 rounding.  ``bf16=True`` rounds inputs,
+weights and hidden activations to bfloat16 (round to nearest even) and is kept
+only as a diagnostic.  History: this oracle was written after the GPU kernels
+of the initializer, unlike the likelihood oracle; its pins stand on their own.
+Shares no code with the CUDA path.
 """
 from __future__ import annotations
 

@@ -65,3 +65,33 @@ def test_adamw_first_step():
     # first step: m_hat = g, v_hat = g^2 -> step lr * sign(g); decay only on matrices
     assert abs(w[ow] - (1 - 1e-3 * 0.1 - 1e-3 * 0.5 / (0.5 + 1e-8))) < 1e-12
     assert abs(w[ob] - (1 - 1e-3 * 0.5 / (0.5 + 1e-8))) < 1e-12
+
+
+def test_head_closed_form():
+    """Head of the initializer: mu_i = mu_cold_i exp(clamp(y_i, -6, 6)) and
+    alpha_ij = (beta_j / M) softplus(y_ij), column j scaled by source j's decay.
+    Checked at points where softplus has a known value: softplus(0) = ln 2,
+    softplus(y) - softplus(-y) = y, softplus(40) = 40 to double precision."""
+    M, B = 2, 3
+    mu_cold = np.array([[0.2, 0.4], [1.0, 3.0], [0.5, 0.5]])
+    beta = np.array([[1.0, 2.0], [0.5, 0.5], [3.0, 1.0]])  # per source
+    y = np.zeros((B, M + M * M))
+    y[1, :M] = [10.0, -10.0]                    # clamped to +-6
+    y[1, M:] = [40.0, -40.0, 3.0, -3.0]
+    y[2, :M] = [0.7, -1.3]
+    y[2, M:] = [1.5, -1.5, 0.0, 0.0]
+    mu, alpha = mlp.head(y, mu_cold, beta, M)
+    np.testing.assert_allclose(mu[0], mu_cold[0], rtol=1e-15)
+    np.testing.assert_allclose(mu[1], [3.0 * np.exp(0.0) * np.exp(6.0) / 3.0, 3.0 * np.exp(-6.0)], rtol=1e-14)
+    np.testing.assert_allclose(mu[2], mu_cold[2] * np.exp([0.7, -1.3]), rtol=1e-14)
+    ln2 = np.log(2.0)
+    np.testing.assert_allclose(alpha[0], [[ln2 / 2, 2 * ln2 / 2], [ln2 / 2, 2 * ln2 / 2]], rtol=1e-15)
+    np.testing.assert_allclose(alpha[1, 0, 0], 0.25 * 40.0, rtol=1e-15)
+    assert 0.0 < alpha[1, 0, 1] <= 0.25 * np.exp(-40.0) * (1 + 1e-12)
+    assert abs((alpha[1, 1, 0] - alpha[1, 1, 1]) / 0.25 - 3.0) <= 1e-13
+    # row 0 of window 2: softplus(1.5) - softplus(-1.5) = 1.5, columns scaled by beta = (3, 1)
+    assert abs(alpha[2, 0, 0] / (3.0 / M) - alpha[2, 0, 1] / (1.0 / M) - 1.5) <= 1e-13
+    np.testing.assert_allclose(alpha[2, 1], [3.0 / M * ln2, 1.0 / M * ln2], rtol=1e-15)
+    # scalar beta broadcasts over sources
+    mu_s, alpha_s = mlp.head(y, mu_cold, np.array([1.0, 0.5, 3.0]), M)
+    np.testing.assert_allclose(alpha_s[0], ln2 / 2, rtol=1e-15)
