@@ -185,7 +185,8 @@ mdhp_status mdhp_fit_batch(mdhp_plan *plan, const mdhp_batch *batch, const mdhp_
                            int32_t *win_status, void *stream);
 
 /* Device time (ms) of the fit kernels of the last mdhp_fit_batch call on this
- * plan, measured with CUDA events recorded on the call's stream around them
+ * plan (the learned initializer's prediction and the length sort excluded),
+ * measured with CUDA events recorded on the call's stream around them
  * (the call synchronises on those events).  Requires timing to have been
  * enabled with mdhp_plan_set_timing(plan, 1) before the call.  Returns <0 if
  * no timing is available. */
@@ -194,7 +195,8 @@ float mdhp_plan_last_fit_ms(mdhp_plan *plan);
 
 /* Number of kernels the last mdhp_fit_batch on this plan launched (length
  * keys, the radix sort counted as one kernel, the range split, the fit
- * kernels; not the learned initializer's), or -1 for a NULL plan. */
+ * kernels, and with init = 2 the learned initializer's features, GEMM and
+ * head kernels), or -1 for a NULL plan. */
 int32_t mdhp_plan_last_launches(const mdhp_plan *plan);
 
 /* Launch shape (for tests, reports and tuning): threads per window and
@@ -216,9 +218,15 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
  * fixed-beta kernels the shared-memory class (none, half, the largest that
  * fits), the feature ring (none; 1x4, 2x3, 2x4, 4x3 steps x stages) and the
  * two-launch split (off; 256 x 1, 256 x 2, 128 x 1, 128 x 2 long threads x CTAs per
- * SM); for the event recursion every built threads-per-chunk split and the
- * staging cutoff (none, the default, the largest that fits).  Each candidate
- * runs tune_iters iterations (<= 0: 20) with tol = 0 after one warm-up run.
+ * SM; not tried when the plan's split was disabled with mdhp_plan_set_split before the
+ * call); for the event recursion every built threads-per-chunk split and the
+ * staging cutoff (none, the default, the largest that fits).  One warm-up
+ * run comes first.  With opts->tol == 0 each candidate runs tune_iters
+ * iterations (<= 0: 20) on every window.  With opts->tol > 0 each candidate
+ * runs the caller's fit to that tolerance (its optimizer, start and patience),
+ * at most min(opts->max_iters, tune_iters) evaluations per window (tune_iters
+ * <= 0: 500): the makespan of such a fit is set by its slowest-converging
+ * windows, which fixed-count runs do not see.
  *   mu, alpha, beta  device, as for mdhp_fit_batch; used as the starting point
  *                    when opts->init == 0 and restored on return
  *   loglik, iters, win_status  device scratch, overwritten
@@ -357,8 +365,13 @@ mdhp_status mdhp_plan_get_pipeline(const mdhp_plan *plan, int32_t *steps_per_sta
  * L2).  Used when the threads per window differ from long_threads and no
  * shared-memory feature class is set.  Default: enabled, 256 threads, 1 per
  * SM.  long_threads 64, 128 or 256; long_ctas_per_sm 1..8.  Results do not
- * depend on the split (each window is fitted by one CTA either way, with the
- * summation order of its block size). */
+ * depend on the split beyond rounding: each window is fitted by one CTA
+ * either way, with the summation order of its block size, and which of the
+ * two launches takes a window near the meeting point depends on timing.  In
+ * a CUDA graph the two launches are sibling nodes with no order between
+ * them; measured on GB300 (65,536 windows, M = 32), a graph replay of a
+ * split fit ran markedly slower than the same call issued on streams, so
+ * capture a plan with the split disabled. */
 mdhp_status mdhp_plan_set_split(mdhp_plan *plan, int32_t enable, int32_t long_threads,
                                 int32_t long_ctas_per_sm);
 mdhp_status mdhp_plan_get_split(const mdhp_plan *plan, int32_t *enable, int32_t *long_threads,
@@ -475,6 +488,20 @@ mdhp_status mdhp_lstm_backward(const mdhp_lstm_dims *dims, const float *x, const
                                const float *dy, float *dz_work, float *dpre_work, float *dx,
                                float *dW, float *dU, float *db, float *dA, float *dBm, float *dC,
                                float *dWy, float *dmu, float *dalpha, float *dbeta, void *stream);
+
+/*
+ * Throughput probe of one arithmetic pipe of the current GPU, for rooflines
+ * (an addition of this library; the paper has no counterpart).  Launches a
+ * kernel that fills every SM to its thread limit with independent dependency
+ * chains of one operation, times it with CUDA events on `stream` (best of
+ * three runs after a warm-up run), synchronises the stream and returns
+ * operations per second in *ops_per_s (and the best time in *ms, nullable):
+ *   what 0  FP32 fused multiply-add, counted as 2 floating-point operations
+ *   what 1  ex2.approx (MUFU)     what 2  lg2.approx (MUFU)     what 3  rcp.approx (MUFU)
+ * Allocates nothing; runs for a few tens of milliseconds.  The clock the GPU
+ * ran at is not controlled: sample it beside the call to compare rates.
+ */
+mdhp_status mdhp_probe_peak(int32_t what, double *ops_per_s, float *ms, void *stream);
 
 /* Text of the last error in this thread (static storage). */
 const char *mdhp_last_error(void);

@@ -84,6 +84,7 @@ SIGNATURES = [
     ("mdhp_plan_set_init_model", ctypes.c_int, [P, P]),
     ("mdhp_lstm_forward", ctypes.c_int, [ctypes.POINTER(MdhpLstmDims)] + [P] * 18),
     ("mdhp_lstm_backward", ctypes.c_int, [ctypes.POINTER(MdhpLstmDims)] + [P] * 30),
+    ("mdhp_probe_peak", ctypes.c_int, [ctypes.c_int32, P, P, P]),
     ("mdhp_last_error", ctypes.c_char_p, []),
     ("mdhp_version", ctypes.c_int32, []),
 ]

@@ -131,6 +131,20 @@ def simulate(M: int, beta_mode: int, mu, alpha, beta, counts, seed: int, stream_
     return DeviceBatch(M, beta_mode, off_d, t[:n], ids[:n], T, None, me), status
 
 
+PEAK_KINDS = ("fp32_fma", "mufu_ex2", "mufu_lg2", "mufu_rcp")
+
+
+def probe_peak(kind: str, stream=None) -> tuple[float, float]:
+    """Measured throughput of one arithmetic pipe of the current GPU
+    (mdhp_probe_peak): (operations per second, best time in ms).  fp32_fma
+    counts an FMA as two floating-point operations."""
+    lib = _lib.load()
+    rate, ms = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    _lib.check(lib.mdhp_probe_peak(PEAK_KINDS.index(kind), ctypes.byref(rate), ctypes.byref(ms),
+                                   _stream(stream)), "mdhp_probe_peak")
+    return rate.value, ms.value
+
+
 @dataclass
 class FitOptions:
     """Mirror of mdhp_fit_opts (defaults as mdhp_fit_opts_default)."""

@@ -88,13 +88,7 @@ WgFn get_wg(int M, int BM) {
   return nullptr;
 }
 
-// Default launch shape per template capacity: threads per window and threads
-// per chunk (sources split across SPL threads), and the longest window staged
-// in shared memory.
-struct Shape {
-  int nt, spl, cutoff;
-};
-static Shape default_shape(int Mt) {
+Shape default_shape(int Mt) {
   switch (Mt) {
     case 4: return {128, 1, 16384};
     case 8: return {128, 2, 12288};
@@ -154,6 +148,11 @@ static mdhp_status check_batch(const mdhp_batch *b, bool matrix_ok = false) {
 }  // namespace mdhp
 
 using namespace mdhp;
+
+namespace mdhp {
+// kernels one mdhp_init_predict call of B windows launches (mdhp_init.cu)
+int init_predict_launches(const mdhp_init_model *model, int B);
+}  // namespace mdhp
 
 struct mdhp_plan {
   int M, Mt, beta_mode, max_windows;
@@ -779,14 +778,11 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   if (B == 0) return MDHP_OK;
   cudaStream_t st = (cudaStream_t)stream;
   mdhp_fit_opts oo = *o;
-  bool t0_done = false;  // the timed region starts before the initializer when it runs
+  int init_launches = 0;
   if (o->init == 2) {  // learned starting point, then the fit from it
-    if (p->timing) {
-      cudaEventRecord(p->ev_t0, st);
-      t0_done = true;
-    }
     const mdhp_status si = mdhp_init_predict(p->model, batch, beta, mu, alpha, stream);
     if (si != MDHP_OK) return si;
+    init_launches = init_predict_launches(p->model, B);
     oo.init = 0;
   }
   o = &oo;
@@ -798,7 +794,9 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   int ev_cap = (bound > 0 && bound < sh.cutoff) ? (int)bound : sh.cutoff;
   const bool need_long = !(bound > 0 && bound <= sh.cutoff);
 
-  p->launches = 3;  // k_lengths, the radix sort (one kernel at these sizes), k_split
+  // k_lengths, the radix sort (one kernel at these sizes), k_split, and the
+  // initializer's kernels when it ran
+  p->launches = 3 + init_launches;
   k_lengths<<<(B + 255) / 256, 256, 0, st>>>(batch->offsets, B, p->keys, p->idx);
   if ((s = cuda_check("k_lengths")) != MDHP_OK) return s;
   size_t tmp = p->sort_tmp_bytes;
@@ -842,7 +840,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     FitArgs ax = a;
     ax.xbuf = p->xbuf;
     const bool any_long = !(xres > 0 && bound <= xres);
-    if (p->timing && !t0_done) cudaEventRecord(p->ev_t0, st);
+    if (p->timing) cudaEventRecord(p->ev_t0, st);
     bool dual_done = false;
     if (any_long && xres == 0 && p->xdual && p->xnt_long != p->xnt) {
       if ((s = launch_dual(p, ax, o->optimizer == 1, st, &dual_done)) != MDHP_OK) return s;
@@ -901,7 +899,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     }
     return MDHP_OK;
   }
-  if (p->timing && !t0_done) cudaEventRecord(p->ev_t0, st);
+  if (p->timing) cudaEventRecord(p->ev_t0, st);
   if (need_long) {
     FitFn fl = get_fit(p->Mt, sh.spl, p->beta_mode, learn, false);
     if (!fl) return fail(MDHP_E_UNSUPPORTED, "no streamed fit kernel for this shape");
@@ -967,8 +965,15 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
   const int B = batch->B;
   if (B == 0) return MDHP_OK;
   mdhp_fit_opts oo = *o;
-  oo.max_iters = tune_iters > 0 ? tune_iters : 20;
-  oo.tol = 0.0;  // every window runs the same number of iterations
+  if (o->tol > 0.0) {
+    // a fit to a tolerance ends when its slowest windows converge, so the
+    // candidates run the caller's fit itself (same tolerance and start),
+    // capped at tune_iters evaluations per window
+    const int cap = tune_iters > 0 ? tune_iters : 500;
+    oo.max_iters = o->max_iters < cap ? o->max_iters : cap;
+  } else {
+    oo.max_iters = tune_iters > 0 ? tune_iters : 20;  // every window runs the same count
+  }
   const bool learn = oo.fit_beta != 0, adam = oo.optimizer == 1;
   const int64_t bound = batch->max_events > 0 ? batch->max_events : p->max_events;
   const int path = (p->use_x && !learn && p->xbuf && bound > 0 && bound <= p->xcap) ? 0 : 1;
@@ -1012,8 +1017,8 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
       }
       if (fit >= 128) cands.push_back({nt, 0, fit / 2 / 32 * 32, 0, 0, 0, 256, 1});
       static const int kSplits[][2] = {{256, 1}, {256, 2}, {128, 1}, {128, 2}};
-      for (const auto &sp : kSplits)
-        if (sp[0] != nt && nt < 256) cands.push_back({nt, 0, 0, 0, 0, 1, sp[0], sp[1]});
+      for (const auto &sp : kSplits)  // a split the caller disabled is not a candidate
+        if (p->xdual && sp[0] != nt && nt < 256) cands.push_back({nt, 0, 0, 0, 0, 1, sp[0], sp[1]});
     } else {
       for (int spl = 1; spl <= 32; spl *= 2) {
         if (nt % spl || !get_fit(p->Mt, spl, p->beta_mode, learn, true) ||

@@ -22,6 +22,14 @@ WgFn get_wg(int M, int BM);
 FitFn get_fitx(int M, int BM, int xm, int nt);
 void record_error(const char *msg);
 
+// Default launch shape of the event-recursion kernels per template capacity
+// Mt: threads per window, threads per chunk (sources split across spl
+// threads), and the longest window staged in shared memory (mdhp_api.cu).
+struct Shape {
+  int nt, spl, cutoff;
+};
+Shape default_shape(int Mt);
+
 #define MDHP_DECLARE_M(MV)                                                   \
   LlgFn get_llg_m##MV(int SPL, int BM, bool learn, bool stage);              \
   FitFn get_fit_m##MV(int SPL, int BM, bool learn, bool stage);              \

@@ -398,8 +398,8 @@ __device__ __forceinline__ bool xpass_pipe(int p0, int p1, int i0, XPipe &pp, co
       }
     }
     __syncthreads();
+    if (sm.ctl[3]) return false;  // fill g is still owed: the drain waits from it on
     ++pp.used;
-    if (sm.ctl[3]) return false;
     if (tid == 0) xpipe_issue<M>(pp, sm);
   }
   if (active) {
@@ -409,7 +409,9 @@ __device__ __forceinline__ bool xpass_pipe(int p0, int p1, int i0, XPipe &pp, co
   return true;
 }
 
-// Waits out the D fills still in flight when a window is done (bounded).
+// Waits out the D fills issued and not yet consumed, pp.used .. pp.used + D - 1
+// (bounded): after the last stage of a window, or after a stage whose fill
+// did not arrive in time (that fill included).
 template <int M>
 __device__ __forceinline__ void xpipe_drain(XPipe &pp, const Sm<M> &sm) {
   for (int d = 0; d < pp.D; ++d) {

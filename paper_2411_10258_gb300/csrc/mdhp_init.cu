@@ -693,6 +693,18 @@ mdhp_status mdhp_init_forward(mdhp_init_model *p, const void *features_bf16, int
   return MDHP_OK;
 }
 
+}  // extern "C"
+
+namespace mdhp {
+// per chunk of max_batch windows: the features, four GEMMs and the head
+int init_predict_launches(const mdhp_init_model *p, int B) {
+  if (!p || B <= 0) return 0;
+  return 6 * ((B + p->max_batch - 1) / p->max_batch);
+}
+}  // namespace mdhp
+
+extern "C" {
+
 mdhp_status mdhp_init_predict(mdhp_init_model *p, const mdhp_batch *batch, const float *beta,
                               float *mu, float *alpha, void *stream) {
   if (!p || !batch || !beta || !mu || !alpha) return init_fail(MDHP_E_ARG, "mdhp_init_predict: NULL argument");

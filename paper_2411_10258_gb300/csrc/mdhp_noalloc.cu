@@ -12,9 +12,12 @@
 // The array lives at file scope in device memory; every GPU that loads the
 // library holds it until the process exits.  Host code may not use its name
 // as a device address: the address is taken once per device with
-// cudaGetSymbolAddress while that device is current, cached, and passed to
-// the kernels.  All calls share the array, so calls that overlap on the GPU
+// cudaGetSymbolAddress while that device is current, cached with the id of
+// the context it belongs to (taken again in a new context, e.g. after
+// cudaDeviceReset), and passed to the kernels.  All calls share the array, so calls that overlap on the GPU
 // (two streams, or two host threads on one device) race on it.
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -33,8 +36,40 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mutex;
 int *g_na_ptr[kMaxDevices] = {};
+unsigned long long g_na_ctx[kMaxDevices] = {};  // id of the context the address belongs to
 
-// Address of the scratch array on the current device (taken once per device).
+// Unique id of the calling thread's current CUDA context (0 if unknown).
+// Context ids are never reused within a process, so an address taken in a
+// context that cudaDeviceReset has since destroyed is never mistaken for one
+// of the new context.  The driver functions are reached through the
+// runtime's entry-point query, so the library needs no link to libcuda.
+unsigned long long current_ctx_id() {
+  using GetCur = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCur get_cur = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q1{}, q2{};
+    void *f1 = nullptr, *f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess && q1 == cudaDriverEntryPointSuccess)
+      get_cur = (GetCur)f1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess && q2 == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f2;
+    cudaGetLastError();
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur && get_id && get_cur(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+    return id;
+  return 0;
+}
+
+// Address of the scratch array on the current device, taken once per device
+// and context (the first call after a cudaDeviceReset takes it again).
 int *na_scratch(mdhp_status *st) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -44,6 +79,9 @@ int *na_scratch(mdhp_status *st) {
     return nullptr;
   }
   std::lock_guard<std::mutex> lock(g_na_mutex);
+  // an address taken in another context (or with no context current, as
+  // after a cudaDeviceReset before the runtime re-creates it) is taken again
+  if (g_na_ptr[dev] && current_ctx_id() != g_na_ctx[dev]) g_na_ptr[dev] = nullptr;
   if (!g_na_ptr[dev]) {
     int *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
@@ -57,6 +95,7 @@ int *na_scratch(mdhp_status *st) {
       return nullptr;
     }
     g_na_ptr[dev] = p;
+    g_na_ctx[dev] = current_ctx_id();
   }
   return g_na_ptr[dev];
 }
@@ -149,12 +188,11 @@ extern "C" mdhp_status mdhp_fit_batch_noalloc(const mdhp_batch *batch, const mdh
   if (B == 0) return MDHP_OK;
   cudaStream_t cs = (cudaStream_t)stream;
 
-  // shape: threads per window and per chunk as the plan-based defaults use
+  // shape: the plan-based entry point's default shape for this width
   const int M = batch->M;
   const int Mt = M <= 4 ? 4 : M <= 8 ? 8 : M <= 16 ? 16 : M <= 32 ? 32 : 64;
-  const int nt = Mt == 64 ? 256 : 128;
-  const int spl = Mt == 4 ? 1 : Mt == 8 ? 2 : Mt == 16 ? 4 : Mt == 32 ? 8 : 16;
-  const int cutoff = Mt == 4 ? 16384 : Mt == 8 ? 12288 : Mt == 16 ? 8192 : Mt == 32 ? 6144 : 8192;
+  const Shape shape = default_shape(Mt);
+  const int nt = shape.nt, spl = shape.spl, cutoff = shape.cutoff;
   const bool learn = o->fit_beta != 0;
   const bool stage = batch->max_events > 0 && batch->max_events <= cutoff;
   FitFn fn = get_fit(Mt, spl, batch->beta_mode, learn, stage);

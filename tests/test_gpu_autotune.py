@@ -104,3 +104,41 @@ def test_recursion_path_tuning_learned_beta(mdhp, wl, tmp_path):
     again.set_path("recursion")
     plan.set_path("recursion")
     assert again.shape() == plan.shape()
+
+
+def test_tolerance_fit_tuning_is_not_slower_than_defaults(mdhp):
+    """For a fit to a tolerance the tuner runs the caller's fit itself (capped
+    evaluations), so the shape it picks is no slower on that fit than the
+    plan's default shape (10 % allowance for timing noise)."""
+    from paper_2411_10258_gb300.workload import workload
+
+    B, M = 16384, 32
+    p = workload.make_params(5, B=B, seed=77)
+    db, sst = mdhp.simulate(M, 0, p["mu"], p["alpha"], p["beta"], p["counts"], seed=77, stream_id=5)
+    assert int((sst != 0).sum().item()) == 0
+    beta0 = torch.from_numpy(p["beta"].astype(np.float32)).cuda()
+    opts = mdhp.FitOptions(optimizer=1, lr=2e-2, max_iters=3000, tol=1e-5, init=1)
+
+    def timed(plan):
+        mu = torch.zeros(B, M, device="cuda")
+        al = torch.zeros(B, M, M, device="cuda")
+        plan.fit(db, opts, mu, al, beta0.clone())
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = plan.fit(db, opts, mu, al, beta0.clone())
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms)), out["loglik"].cpu().numpy()
+
+    plan_d = mdhp.Plan(M, 0, B, int(p["counts"].max()))
+    plan_t = mdhp.Plan(M, 0, B, int(p["counts"].max()))
+    choice = plan_t.autotune(db, opts, torch.zeros(B, M, device="cuda"), torch.zeros(B, M, M, device="cuda"),
+                             beta0.clone(), tune_iters=400)
+    ms_d, ll_d = timed(plan_d)
+    ms_t, ll_t = timed(plan_t)
+    print("default", ms_d, "tuned", ms_t, choice)
+    assert ms_t <= 1.10 * ms_d, (ms_t, ms_d, choice)
+    assert np.all(np.isfinite(ll_t))

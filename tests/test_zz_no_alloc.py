@@ -2,7 +2,9 @@
 device memory (pooled framework allocators, no-allocation-after-start-up
 deployments).  Called through the C ABI and checked against the plan-based
 mdhp_fit_batch on the same inputs, twice in a row, since every call shares the
-library's fixed scratch array.  Collected last on purpose."""
+library's fixed scratch array: windows staged in shared memory, the same
+windows streamed from device memory, and M = 64 with beta per source learned.
+Collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -19,6 +21,44 @@ def _p(x):
     return ctypes.c_void_p(x.data_ptr())
 
 
+def _cases(wl):
+    """(name, host batch, beta, fit options, max_events override):
+    the staged recursion at M = 16 (events in shared memory), the same windows
+    streamed from device memory (no stated bound), and M = 64 with beta per
+    source learned (streamed)."""
+    import paper_2411_10258_gb300 as mdhp
+
+    bt = wl.make_workload(2, B=48, seed=909)
+    yield ("staged_m16", bt, bt.beta, mdhp.FitOptions(optimizer=1, max_iters=40, lr=5e-3, init=1), None)
+    yield ("streamed_m16", bt, bt.beta, mdhp.FitOptions(optimizer=1, max_iters=40, lr=5e-3, init=1), 0)
+    rng = np.random.default_rng(31)
+    M, B = 64, 6
+    betas = rng.uniform(0.5, 2.0, (B, M))
+    mu_t, a_t = wl.sample_params(rng, B, M, 1, betas, rng.uniform(0.2, 0.8, B))
+    bt64 = wl.simulate(M, 1, mu_t, a_t, betas, np.array([900, 4000, 2500, 300, 7000, 1200]), 19, 92)
+    yield ("learned_beta_m64", bt64, np.full((B, M), 1.0, np.float32),
+           mdhp.FitOptions(optimizer=1, max_iters=15, lr=2e-3, fit_beta=1, init=1), 0)
+
+
+def _noalloc_call(lib, _lib, db, opts, beta):
+    B, M = db.B, db.M
+    mu = torch.zeros(B, M, device="cuda")
+    alpha = torch.zeros(B, M, M, device="cuda")
+    b = beta.clone()
+    ll = torch.empty(B, dtype=torch.float64, device="cuda")
+    it = torch.empty(B, dtype=torch.int32, device="cuda")
+    st = torch.empty(B, dtype=torch.int32, device="cuda")
+    cb = db.c_struct()
+    co = opts.c_struct()
+    rc = lib.mdhp_fit_batch_noalloc(ctypes.byref(cb), ctypes.byref(co), _p(mu), _p(alpha), _p(b),
+                                    _p(ll), _p(it), _p(st),
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _lib.check(rc, "mdhp_fit_batch_noalloc")
+    torch.cuda.synchronize()
+    return (mu.cpu().numpy(), alpha.cpu().numpy(), b.cpu().numpy(), ll.cpu().numpy(), it.cpu().numpy(),
+            st.cpu().numpy())
+
+
 def test_noalloc_matches_plan_fit_twice(wl):
     import paper_2411_10258_gb300 as mdhp
     from paper_2411_10258_gb300 import _lib
@@ -26,47 +66,36 @@ def test_noalloc_matches_plan_fit_twice(wl):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     lib = _lib.load()
-    bt = wl.make_workload(2, B=48, seed=909)
-    M, B = bt.M, bt.B
-    db = mdhp.DeviceBatch.from_host(bt, "cuda")
-    beta = torch.from_numpy(bt.beta).cuda()
-    opts = mdhp.FitOptions(optimizer=1, max_iters=40, lr=5e-3, init=1)
-
-    plan = mdhp.Plan(M, 0, B, int(bt.counts.max()))
-    ref_mu = torch.zeros(B, M, device="cuda")
-    ref_alpha = torch.zeros(B, M, M, device="cuda")
-    ref = plan.fit(db, opts, ref_mu, ref_alpha, beta.clone())
-    torch.cuda.synchronize()
-
-    runs = []
-    for _ in range(2):
-        mu = torch.zeros(B, M, device="cuda")
-        alpha = torch.zeros(B, M, M, device="cuda")
-        b = beta.clone()
-        ll = torch.empty(B, dtype=torch.float64, device="cuda")
-        it = torch.empty(B, dtype=torch.int32, device="cuda")
-        st = torch.empty(B, dtype=torch.int32, device="cuda")
-        cb = db.c_struct()
-        co = opts.c_struct()
-        rc = lib.mdhp_fit_batch_noalloc(ctypes.byref(cb), ctypes.byref(co), _p(mu), _p(alpha), _p(b),
-                                        _p(ll), _p(it), _p(st),
-                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-        _lib.check(rc, "mdhp_fit_batch_noalloc")
+    for name, bt, beta_h, opts, max_events in _cases(wl):
+        M, B = bt.M, bt.B
+        db = mdhp.DeviceBatch.from_host(bt, "cuda", max_events=max_events)
+        beta = torch.from_numpy(np.ascontiguousarray(beta_h, dtype=np.float32)).cuda()
+        plan = mdhp.Plan(M, bt.beta_mode, B, db.max_events)
+        plan.set_path("recursion")  # the kernels the allocation-free call runs
+        ref_mu = torch.zeros(B, M, device="cuda")
+        ref_alpha = torch.zeros(B, M, M, device="cuda")
+        ref_beta = beta.clone()
+        ref = plan.fit(db, opts, ref_mu, ref_alpha, ref_beta)
         torch.cuda.synchronize()
-        runs.append((mu.cpu().numpy(), alpha.cpu().numpy(), ll.cpu().numpy(), it.cpu().numpy(),
-                     st.cpu().numpy()))
-
-    r_mu, r_alpha = ref["mu"].cpu().numpy(), ref["alpha"].cpu().numpy()
-    r_ll, r_it, r_st = ref["loglik"].cpu().numpy(), ref["iters"].cpu().numpy(), ref["status"].cpu().numpy()
-    for mu, alpha, ll, it, st in runs:
-        np.testing.assert_array_equal(st, r_st)
-        np.testing.assert_array_equal(it, r_it)
-        assert np.all(np.abs(ll - r_ll) <= LL_RTOL * np.abs(r_ll))
-        for w in range(B):
-            assert np.all(np.abs(mu[w] - r_mu[w]) <= P_RTOL * np.abs(r_mu[w]).max())
-            assert np.all(np.abs(alpha[w] - r_alpha[w]) <= P_RTOL * np.abs(r_alpha[w]).max() + 1e-30)
-    # the two calls in a row agree with each other exactly (same kernel, same inputs)
-    np.testing.assert_array_equal(runs[0][2], runs[1][2])
+        runs = [_noalloc_call(lib, _lib, db, opts, beta) for _ in range(2)]
+        r_mu, r_alpha, r_beta = ref_mu.cpu().numpy(), ref_alpha.cpu().numpy(), ref_beta.cpu().numpy()
+        r_ll, r_it, r_st = ref["loglik"].cpu().numpy(), ref["iters"].cpu().numpy(), ref["status"].cpu().numpy()
+        for mu, alpha, be, ll, it, st in runs:
+            np.testing.assert_array_equal(st, r_st, err_msg=name)
+            np.testing.assert_array_equal(it, r_it, err_msg=name)
+            assert np.all(np.abs(ll - r_ll) <= LL_RTOL * np.abs(r_ll)), name
+            for w in range(B):
+                assert np.all(np.abs(mu[w] - r_mu[w]) <= P_RTOL * np.abs(r_mu[w]).max()), (name, w)
+                assert np.all(np.abs(alpha[w] - r_alpha[w]) <= P_RTOL * np.abs(r_alpha[w]).max() + 1e-30), \
+                    (name, w)
+                assert np.all(np.abs(be[w] - r_beta[w]) <= P_RTOL * np.abs(r_beta[w]).max()), (name, w)
+        # the two calls in a row agree with each other exactly (same kernel, same
+        # inputs) where the d/dalpha sums are private per thread (M <= 32); at
+        # M = 64 they are shared-memory atomics, whose order varies run to run
+        if M <= 32:
+            np.testing.assert_array_equal(runs[0][3], runs[1][3], err_msg=name)
+        else:
+            assert np.all(np.abs(runs[0][3] - runs[1][3]) <= LL_RTOL * np.abs(runs[1][3])), name
 
 
 def test_noalloc_rejects_oversized_batch():
