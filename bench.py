@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--chunk-threads", type=int, default=0, help="--workload 5fixed: threads per chunk")
     ap.add_argument("--cutoff", type=int, default=-1, help="--workload 5fixed: shared-memory cutoff (events)")
     ap.add_argument("--no-split", action="store_true", help="--workload 5fixed: one launch, no split")
+    ap.add_argument("--split-threads", type=int, default=0,
+                    help="--workload 5fixed: threads of the long-window launch of the split")
     ap.add_argument("--no-graph", action="store_true", help="warm arm as plain calls, not a CUDA graph")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline only: skip the fixed-iteration lines, the reference optimum and e2e")
@@ -848,11 +850,11 @@ def run_headline(args):
         plans[name] = Plan(M, 0, B, int(p["counts"].max()))
         if name == "warm":
             model.attach(plans[name])
-            if not args.no_graph:
-                # the two-launch split needs its launches to reach the SMs in
-                # issue order, which a graph's sibling nodes do not keep: the
-                # graph arm is tuned over single-launch shapes
-                plans[name].set_split(False)
+        # both arms are tuned over single-launch shapes: the two-launch split
+        # needs its launches to reach the SMs in issue order, which the warm
+        # arm's graph (sibling nodes) does not keep, and the cold arm keeps
+        # the same kernel family so the two arms differ only in their start
+        plans[name].set_split(False)
         opts[name] = FitOptions(tol=args.tol, optimizer=HEADLINE_OPTS["optimizer"], lr=args.lr,
                                 max_iters=HEADLINE_OPTS["max_iters"], **kw)
         tuned[name] = None if args.no_autotune else plans[name].autotune(
@@ -905,9 +907,15 @@ def run_headline(args):
             for i in range(args.steps):
                 flush.fill_(float(i))
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                if args.profile_step and i == 0:  # one step per arm as a profiler range
+                    torch.cuda.synchronize()
+                    torch.cuda.cudart().cudaProfilerStart()
                 e0.record(stream)
                 step(name)
                 e1.record(stream)
+                if args.profile_step and i == 0:
+                    torch.cuda.synchronize()
+                    torch.cuda.cudart().cudaProfilerStop()
                 if name == "cold":
                     res[name]["kern_ms"].append(plans[name].last_fit_ms())
                 res[name]["ev"] = res[name].get("ev", []) + [(e0, e1)]
@@ -955,30 +963,46 @@ def run_headline(args):
     torch.cuda.synchronize()
     res["warm"]["predict_ms"] = e0.elapsed_time(e1)
 
-    # roofline of the dominant kernel: the decoupled fit (k_fit_x, its two
-    # concurrent launches timed together) in the cold arm's timed steps
+    # roofline of the dominant kernel: the decoupled fit (k_fit_x) in the cold
+    # arm's timed steps.  Algorithmic work per event-iteration: the FMA count
+    # of the method's recursion (decays, the lambda dot product, the d/dalpha
+    # row and the compensated sums: 3M + 4 FMA = 2(3M + 4) FLOP); the work
+    # the decoupled kernel executes (the decays hoisted out: 4M + 8 FLOP) is
+    # reported beside it.
     peak, src = fp32_peak_from(peaks)
     kern = float(np.mean(res["cold"]["kern_ms"]))
     ev_it = res["cold"]["event_iterations"]
-    achieved = ev_it * flops_per_event_iter(M) / (kern / 1e3) / 1e12
+    alg_flops = 2 * recursion_fma_per_event_iter(M)
+    achieved = ev_it * alg_flops / (kern / 1e3) / 1e12
+    impl = ev_it * flops_per_event_iter(M) / (kern / 1e3) / 1e12
     mufu_rate = min(peaks["mufu_lg2"], peaks["mufu_rcp"])
+    feat_gbs = ev_it * feature_bytes_per_event_iter(M) / (kern / 1e3) / 1e9
+    hbm_peak, hbm_src = measured_peaks()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "traffic_note": "no DRAM capture of this kernel on this workload yet",
-                "kernel": "k_fit_x<32>: decoupled features, two concurrent launches over one "
-                          "length-sorted queue, cold arm; time = CUDA events on the calling stream "
-                          "around both launches (fork to join), mean over the timed steps",
+                "frac": achieved / peak, "traffic": args.traffic,
+                "traffic_note": "DRAM read + write of one fit, scaled from an ncu capture of the same "
+                                "kernel and launch shape on 8,192 windows by event-iterations "
+                                "(summary under profiles/)" if args.traffic else
+                                "no DRAM capture of this kernel and shape given (--traffic)",
+                "kernel": "k_fit_x<32> (decoupled features, one persistent launch), cold arm; time = "
+                          "CUDA events on the calling stream around the fit kernels, mean over the "
+                          "timed steps",
                 "fit_kernel_ms": kern, "event_iterations_per_fit": ev_it,
-                "flops_per_event_iteration": flops_per_event_iter(M),
+                "flops_per_event_iteration": alg_flops,
+                "flops_note": f"{recursion_fma_per_event_iter(M)} FMA per event-iteration: the method's "
+                              "recursion (decay of the M states, lambda dot product, d/dalpha row, "
+                              "compensated sums)",
                 "peak_source": src,
-                "frac_at_recursion_count": ev_it * 2 * recursion_fma_per_event_iter(M) / (kern / 1e3)
-                                           / 1e12 / peak,
-                "recursion_count_note": f"{recursion_fma_per_event_iter(M)} FMA per event-iteration "
-                                        "(decays + dot + d/dalpha + sums of the plain recursion; the "
-                                        "decoupled kernel hoists the decays, so this credits work it "
-                                        "does not do)",
+                "implemented_flops_per_event_iteration": flops_per_event_iter(M),
+                "frac_implemented_work": impl / peak,
                 "mufu_frac": ev_it * MUFU_PER_EVENT_ITER / (kern / 1e3) / mufu_rate,
-                "mufu_peak_ops_per_s": mufu_rate}
+                "mufu_peak_ops_per_s": mufu_rate,
+                "feature_read_gbs": feat_gbs,
+                "feature_read_frac_of_hbm": feat_gbs / float(hbm_peak.get("hbm_gbs", 6800.0)),
+                "hbm_peak_source": f"{hbm_src}: MEASURED_PEAKS copy bandwidth",
+                "measured_limiter": "HBM: at M = 32 the stored features (128 B per event-iteration) "
+                                    "of the windows in flight exceed L2 and are re-read from HBM "
+                                    "at every iteration (profiles/)"}
     line = {"metric": METRIC, "value": res["warm"]["fits_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["warm"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -1187,6 +1211,8 @@ def run_fixed_headline(args):
         plan.set_shape(args.threads, args.chunk_threads or spl, cut if args.cutoff < 0 else args.cutoff)
     if args.no_split:
         plan.set_split(False)
+    elif args.split_threads:
+        plan.set_split(True, args.split_threads, 1)
     beta = torch.from_numpy(p["beta"].astype(np.float32)).to(dev)
     opts = FitOptions(optimizer=HEADLINE_OPTS["optimizer"], lr=args.lr, max_iters=args.iters, init=1)
     plan.set_timing(True)
