@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--beta", type=float, default=1.0, help="beta of --workload 2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="5", choices=["2", "3", "4", "5", "5fixed", "6", "attack", "lstm"],
+    ap.add_argument("--workload", default="5", choices=["2", "3", "4", "5", "5fixed", "6", "attack", "lstm", "gemm"],
                     help="5 (default): warm vs cold fits to tolerance; 2: fixed-iteration fits")
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--lr", type=float, default=HEADLINE_LR,
@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--chunk-threads", type=int, default=0, help="--workload 5fixed: threads per chunk")
     ap.add_argument("--cutoff", type=int, default=-1, help="--workload 5fixed: shared-memory cutoff (events)")
     ap.add_argument("--no-split", action="store_true", help="--workload 5fixed: one launch, no split")
+    ap.add_argument("--event-ring", action="store_true",
+                    help="--workload 3: streamed events through the bulk-copy ring, not global loads")
     ap.add_argument("--split-threads", type=int, default=0,
                     help="--workload 5fixed: threads of the long-window launch of the split")
     ap.add_argument("--no-graph", action="store_true", help="warm arm as plain calls, not a CUDA graph")
@@ -535,6 +537,7 @@ def run_long_learned(args):
     B, M = db.B, 64
     beta0 = torch.from_numpy(p["beta"]).float().to(dev)
     plan = Plan(M, 1, B, 0)
+    plan.set_event_ring(args.event_ring)
     opts = FitOptions(optimizer=1, max_iters=args.iters, lr=1e-2, init=1, fit_beta=1)
     mu = torch.zeros(B, M, device=dev)
     al = torch.zeros(B, M, M, device=dev)
@@ -562,7 +565,8 @@ def run_long_learned(args):
             "config": {"workload": f"512 windows x M=64, counts log-uniform[2e4,1e5] "
                                    f"({int(p['counts'].sum())} events), beta per source learned, "
                                    f"projected Adam lr 1e-2, {args.iters} iterations",
-                       "shape": plan.shape()},
+                       "shape": plan.shape(),
+                       "event_ring": bool(args.event_ring)},
             "llg_events_per_s": ev_it / (avg / 1000.0),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
@@ -1227,6 +1231,68 @@ def run_fixed_headline(args):
                           "invalid_windows": int((out["status"] != 0).sum().item())}), flush=True)
 
 
+def run_gemm(args):
+    """The learned initializer's largest layer product: 4,096 windows' features
+    (K = 8,256 for M = 16) times the 256 x 8,256 first-layer weights, BF16 with
+    FP32 accumulation, bias and ReLU, FP32 and BF16 outputs (mdhp_gemm_bf16),
+    on the tensor-core engine (tcgen05) and on the warp-level MMA engine.  Each
+    launch is timed alone with CUDA events after a 256 MB write that flushes
+    L2; value = TFLOP/s of the tensor-core engine (2 M N K per launch)."""
+    import torch
+
+    from paper_2411_10258_gb300.api import gemm_bf16, gemm_check
+
+    dev = torch.device("cuda", 0)
+    M, N, K = 4096, 256, 8256
+    g = torch.Generator(device=dev).manual_seed(5)
+    A = (torch.rand(M, K, generator=g, device=dev) * 2 - 1).to(torch.bfloat16)
+    W = ((torch.rand(N, K, generator=g, device=dev) * 2 - 1) / np.sqrt(K)).to(torch.bfloat16)
+    bias = torch.zeros(N, device=dev)
+    C = torch.empty(M, N, device=dev)
+    Cb = torch.empty(M, N, dtype=torch.bfloat16, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    peaks, src = measured_peaks()
+    flops = 2.0 * M * N * K
+    res = {}
+    sampler = ClockSampler(0, os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None,
+                           name="gemm")
+    with sampler:
+        for name, engine in (("tcgen05", 0), ("mma_sync", 1)):
+            for _ in range(max(args.warmup, 3)):
+                gemm_bf16(A, W, M, N, K, bias=bias, relu=True, C=C, C_bf16=Cb, engine=engine)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(max(args.steps, 10)):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gemm_bf16(A, W, M, N, K, bias=bias, relu=True, C=C, C_bf16=Cb, engine=engine)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            if gemm_check() != 0:
+                raise RuntimeError("tensor-core GEMM wait timed out")
+            med = float(np.median(ms))
+            res[name] = {"ms_median": med, "ms_min": float(min(ms)), "tflops": flops / (med * 1e-3) / 1e12}
+    ref = A[:64].double() @ W.double().t()
+    err = float(((C[:64].double() - torch.clamp(ref, min=0)).abs().max()))
+    tc = res["tcgen05"]
+    peak = float(peaks["bf16_tflops"])
+    print(json.dumps({
+        "metric": "initializer first-layer GEMM throughput (BF16, FP32 accumulate)",
+        "value": tc["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": max(args.steps, 10),
+        "warmup": max(args.warmup, 3), "ms_per_step": tc["ms_median"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"M={M} windows x K={K} features -> N={N} hidden (bias, ReLU, FP32+BF16 out)",
+                   "l2": "flushed (256 MB write) before every timed launch"},
+        "roofline": {"bound": "tensor", "achieved": tc["tflops"], "peak": peak, "unit": "TFLOP/s",
+                     "frac": tc["tflops"] / peak, "traffic": None,
+                     "kernel": "k_gemm_tc (tcgen05.mma, TMEM accumulators) + k_gemm_finish",
+                     "peak_source": f"{src}: MEASURED_PEAKS bf16 burst (cuBLAS)"},
+        "engines": res, "max_abs_err_first_64_rows": err,
+        "gpu_launches": None, "clocks": sampler.summary()}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1243,6 +1309,8 @@ def main():
         run_attacks(args)
     elif args.workload == "lstm":
         run_lstm(args)
+    elif args.workload == "gemm":
+        run_gemm(args)
     else:  # 2, or 6 (the same with the full decay matrix)
         run_ours(args)
 

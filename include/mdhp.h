@@ -326,6 +326,41 @@ mdhp_status mdhp_init_backward(mdhp_init_model *model, const void *features_bf16
 mdhp_status mdhp_init_set_grads(mdhp_init_model *model, const float *src, void *stream);
 mdhp_status mdhp_init_apply(mdhp_init_model *model, float lr, float weight_decay, void *stream);
 
+/* Engine of the model's matrix products: 0 (default) the tensor-core GEMM
+ * of mdhp_gemm_bf16 (tcgen05) wherever its operand layouts apply, else the
+ * warp-level MMA kernel; 1 the warp-level MMA kernel (mma.sync) for every
+ * product.  Errors: engine outside 0..1 (MDHP_E_ARG). */
+mdhp_status mdhp_init_model_set_gemm(mdhp_init_model *model, int32_t engine);
+
+/*
+ * BF16 matrix product with FP32 accumulation, the initializer's layer GEMM
+ * (an addition of this library; the paper has no initializer):
+ *   C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n], then ReLU if relu)      accumulate = 0
+ *   C[m][n] += sum_k A(m,k) B(k,n)                                    accumulate = 1
+ * A(m,k) = A[m*lda + k] (a_mn = 0, K contiguous) or A[k*lda + m] (a_mn = 1);
+ * B(k,n) = B[n*ldb + k] (b_mn = 0, K contiguous) or B[k*ldb + n] (b_mn = 1);
+ * all device pointers, BF16 operands, row-major outputs with pitch ldc: C
+ * (FP32, nullable when accumulate = 0 and C_bf16 is given) and C_bf16 (BF16
+ * copy of the result, nullable; ignored when accumulate = 1).
+ * engine 0: fifth-generation tensor cores (tcgen05.mma, accumulators in tensor
+ * memory; 128 x up-to-256 tiles, K split over CTAs when the tiles alone do not
+ * fill the GPU, in which case C is required and holds the partial sums).  It
+ * needs 16-byte aligned A and B, lda and ldb multiples of 8, K a multiple of
+ * 8 and, for an M/N-contiguous operand, M (resp. N) a multiple of 8; other
+ * shapes return MDHP_E_UNSUPPORTED.  engine 1: warp-level MMA (mma.sync) on
+ * 64 x 64 tiles, any layout.  Asynchronous on `stream`.  Errors: NULL
+ * operands, sizes < 1, engine outside 0..1 (MDHP_E_ARG).
+ */
+mdhp_status mdhp_gemm_bf16(const void *A, int64_t lda, int32_t a_mn, const void *B, int64_t ldb,
+                           int32_t b_mn, int32_t M, int32_t N, int32_t K, const float *bias,
+                           int32_t relu, float *C, void *C_bf16, int64_t ldc, int32_t accumulate,
+                           int32_t engine, void *stream);
+
+/* Synchronises the device and reports (then clears) the number of
+ * tensor-core GEMM CTAs whose bounded waits gave up since the last call
+ * (their tiles were not written). */
+mdhp_status mdhp_gemm_check(int32_t *timeouts);
+
 /* Attach a trained model to a plan: mdhp_fit_batch with opts->init == 2 then
  * predicts the starting point with it (the plan does not own the model). */
 mdhp_status mdhp_plan_set_init_model(mdhp_plan *plan, mdhp_init_model *model);
@@ -354,6 +389,33 @@ mdhp_status mdhp_plan_set_path(mdhp_plan *plan, int32_t path);
 mdhp_status mdhp_plan_set_pipeline(mdhp_plan *plan, int32_t steps_per_stage, int32_t stages);
 mdhp_status mdhp_plan_get_pipeline(const mdhp_plan *plan, int32_t *steps_per_stage,
                                    int32_t *stages);
+
+/* Streamed events of the event recursion (windows without a stated bound, or
+ * longer than the staging cutoff; beta learned, or MDHP_PATH_RECURSION):
+ * enable = 1 delivers each chunk's events to the recursion through a ring of
+ * two shared-memory stages of 128 events per chunk, filled by bulk
+ * asynchronous copies (cp.async.bulk, CTA-local) running a stage ahead, with
+ * bounded waits; enable = 0 (default) reads them from global memory through
+ * the read-only cache.  The ring is used
+ * when the batch's t and id arrays are 16-byte aligned and there are no
+ * per-event weights; otherwise, or when it does not fit the block's shared
+ * memory, events are read from global memory.  Results do not depend on it
+ * beyond the run-to-run rounding of learned-beta fits. */
+mdhp_status mdhp_plan_set_event_ring(mdhp_plan *plan, int32_t enable);
+
+/* Bound of a consumer's wait on a bulk-copy ring (the feature ring of
+ * mdhp_plan_set_pipeline and the event ring of mdhp_plan_set_event_ring):
+ * polls = 0 (default) waits up to 2^22 suspending polls, far beyond any
+ * copy's latency; polls > 0 gives up after that many non-blocking tests.
+ * A feature-ring wait that gives up reports the window as MDHP_E_TIMEOUT
+ * (loglik NaN, parameters not written back); an event-ring wait that gives
+ * up switches that CTA's remaining chunks to global-memory reads (same
+ * results).  Either way the copies already in flight are waited out with the
+ * full bound before the shared memory is used again, and a CTA whose drain
+ * also gives up reports its later windows as MDHP_E_TIMEOUT without touching
+ * the ring.  Small bounds exist to exercise these paths; errors: polls < 0
+ * (MDHP_E_ARG). */
+mdhp_status mdhp_plan_set_wait_limit(mdhp_plan *plan, int32_t polls);
 
 /* Split of the decoupled kernels' streamed windows over two concurrent
  * launches that share one length-sorted queue from its two ends: the longest

@@ -85,6 +85,13 @@ SIGNATURES = [
     ("mdhp_lstm_forward", ctypes.c_int, [ctypes.POINTER(MdhpLstmDims)] + [P] * 18),
     ("mdhp_lstm_backward", ctypes.c_int, [ctypes.POINTER(MdhpLstmDims)] + [P] * 30),
     ("mdhp_probe_peak", ctypes.c_int, [ctypes.c_int32, P, P, P]),
+    ("mdhp_plan_set_event_ring", ctypes.c_int, [P, ctypes.c_int32]),
+    ("mdhp_plan_set_wait_limit", ctypes.c_int, [P, ctypes.c_int32]),
+    ("mdhp_init_model_set_gemm", ctypes.c_int, [P, ctypes.c_int32]),
+    ("mdhp_gemm_bf16", ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, P, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32,
+                                      P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P]),
+    ("mdhp_gemm_check", ctypes.c_int, [P]),
     ("mdhp_last_error", ctypes.c_char_p, []),
     ("mdhp_version", ctypes.c_int32, []),
 ]

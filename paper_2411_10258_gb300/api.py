@@ -145,6 +145,31 @@ def probe_peak(kind: str, stream=None) -> tuple[float, float]:
     return rate.value, ms.value
 
 
+def gemm_bf16(A: torch.Tensor, B: torch.Tensor, M: int, N: int, K: int, a_mn: bool = False,
+              b_mn: bool = False, bias: torch.Tensor | None = None, relu: bool = False,
+              C: torch.Tensor | None = None, C_bf16: torch.Tensor | None = None, accumulate: bool = False,
+              engine: int = 0, stream=None):
+    """C (+)= A B (mdhp_gemm_bf16).  A: bfloat16 [M, K] (a_mn False) or [K, M];
+    B: bfloat16 [N, K] (b_mn False) or [K, N]; C float32 [M, N] and/or C_bf16
+    bfloat16 [M, N] (row pitch N).  engine 0: tcgen05 tensor cores, 1: mma.sync."""
+    lib = _lib.load()
+    lda = A.shape[1]
+    ldb = B.shape[1]
+    _lib.check(lib.mdhp_gemm_bf16(_ptr(A), lda, int(a_mn), _ptr(B), ldb, int(b_mn), M, N, K,
+                                  _ptr(bias) if bias is not None else None, int(relu),
+                                  _ptr(C) if C is not None else None,
+                                  _ptr(C_bf16) if C_bf16 is not None else None, N, int(accumulate),
+                                  engine, _stream(stream)), "mdhp_gemm_bf16")
+
+
+def gemm_check() -> int:
+    """Synchronise; tensor-core GEMM CTAs whose bounded waits gave up since the last call."""
+    lib = _lib.load()
+    n = ctypes.c_int32(0)
+    _lib.check(lib.mdhp_gemm_check(ctypes.byref(n)), "mdhp_gemm_check")
+    return n.value
+
+
 @dataclass
 class FitOptions:
     """Mirror of mdhp_fit_opts (defaults as mdhp_fit_opts_default)."""
@@ -242,6 +267,15 @@ class Plan:
                     threads_per_chunk=chosen[2], cutoff=chosen[3], pipe_steps=chosen[4],
                     pipe_stages=chosen[5], split=bool(chosen[6]), split_threads=chosen[7],
                     split_ctas=chosen[8], ms=best.value)
+
+    def set_event_ring(self, enable: bool):
+        """Streamed events through the bulk-copy ring (mdhp_plan_set_event_ring)."""
+        _lib.check(self.lib.mdhp_plan_set_event_ring(self.h, 1 if enable else 0),
+                   "mdhp_plan_set_event_ring")
+
+    def set_wait_limit(self, polls: int):
+        """Bound of the bulk-copy rings' consumer waits (mdhp_plan_set_wait_limit); 0 = default."""
+        _lib.check(self.lib.mdhp_plan_set_wait_limit(self.h, polls), "mdhp_plan_set_wait_limit")
 
     def set_pipeline(self, steps_per_stage: int, stages: int):
         """Feature ring of the decoupled kernels (mdhp_plan_set_pipeline); stages=0: none."""
@@ -437,6 +471,10 @@ class InitModel:
         self.set_grads(g)
         self.apply(lr, weight_decay)
         return loss
+
+    def set_gemm(self, engine: int):
+        """0: tensor-core (tcgen05) products where they apply; 1: mma.sync for all."""
+        _lib.check(self.lib.mdhp_init_model_set_gemm(self.h, engine), "mdhp_init_model_set_gemm")
 
     def attach(self, plan: "Plan"):
         """Use this model for FitOptions(init=2) fits of `plan`."""

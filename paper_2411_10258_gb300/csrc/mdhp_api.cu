@@ -181,6 +181,12 @@ struct mdhp_plan {
   // of the register file holds; fewer windows in flight keeps their features
   // in L2.  0 = one launch of xnt threads.
   int xdual = 1, xnt_long = 256, xcta_long = 1;
+  // recursion fit: streamed events reach pass 2 through the bulk-copy ring
+  // (off by default: the recursion spends ~2,000 instructions per event on
+  // 6 bytes of event data, and the ring's shared-memory reads measured slower
+  // than cached global loads)
+  int ev_ring = 0;
+  uint32_t wait_polls = 0;           // consumer waits on the bulk-copy rings (0: default bound)
   mdhp_init_model *model = nullptr;  // learned initializer (not owned)
   std::string cache;                 // autotune cache file ("" = none)
   int launches = 0;                  // kernel launches of the last mdhp_fit_batch
@@ -560,7 +566,9 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
   ok &= cudaMalloc(&p->idx, sizeof(int) * max_windows) == cudaSuccess;
   ok &= cudaMalloc(&p->order, sizeof(int) * max_windows) == cudaSuccess;
   ok &= cudaMalloc(&p->ctl, sizeof(int) * 16) == cudaSuccess;
-  p->pstride = (p->Mt + p->Mt * p->Mt + p->Mt + 63) / 64 * 64;
+  // per-CTA device slot of the recursion fit: theta_{k-1}, the gradient
+  // buffer and the two Adam moments, pstride / 4 floats each
+  p->pstride = 4 * ((p->Mt + p->Mt * p->Mt + p->Mt + 63) / 64 * 64);
   p->pslots = num_sms() * 16;
   ok &= cudaMalloc(&p->pbuf, sizeof(float) * (size_t)p->pslots * p->pstride) == cudaSuccess;
   if (ok) {
@@ -677,6 +685,19 @@ mdhp_status mdhp_plan_set_path(mdhp_plan *p, int32_t path) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
   if (path != MDHP_PATH_AUTO && path != MDHP_PATH_RECURSION) return fail(MDHP_E_ARG, "path %d", path);
   p->use_x = path == MDHP_PATH_AUTO ? 1 : 0;
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_plan_set_event_ring(mdhp_plan *p, int32_t enable) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  p->ev_ring = enable ? 1 : 0;
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_plan_set_wait_limit(mdhp_plan *p, int32_t polls) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  if (polls < 0) return fail(MDHP_E_ARG, "polls %d < 0", polls);
+  p->wait_polls = (uint32_t)polls;
   return MDHP_OK;
 }
 
@@ -825,6 +846,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   a.patience = o->patience; a.init = o->init; a.lr = o->lr; a.mu_floor = o->mu_floor;
   a.alpha_floor = o->alpha_floor; a.beta_floor = o->beta_floor; a.b1 = o->adam_b1;
   a.b2 = o->adam_b2; a.eps = o->adam_eps; a.tol = o->tol;
+  a.wait_polls = p->wait_polls;
 
   int xres = p->xres;
   if (xpath && xres > 0) {  // the largest class that fits this block size
@@ -909,8 +931,18 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
     al.ev_cap = 0;
     al.pbuf = p->pbuf;
     al.pstride = p->pstride;
+    al.ring = (p->ev_ring && !batch->weights && ((uintptr_t)batch->t & 15) == 0 &&
+               ((uintptr_t)batch->id & 15) == 0)
+                  ? 1
+                  : 0;
+    al.n_total = batch->n_events;
     al.carve = make_carve(p->Mt, sh.nt, sh.spl, 0, batch->weights != nullptr, learn,
-                          o->optimizer == 1, true, use_priv(p->Mt), false);
+                          o->optimizer == 1, true, use_priv(p->Mt), false, al.ring != 0);
+    if (al.ring && al.carve.total > max_dyn_smem()) {  // no room for the ring: read global memory
+      al.ring = 0;
+      al.carve = make_carve(p->Mt, sh.nt, sh.spl, 0, batch->weights != nullptr, learn,
+                            o->optimizer == 1, true, use_priv(p->Mt), false);
+    }
     if ((s = prepare_kernel((const void *)fl, al.carve.total)) != MDHP_OK) return s;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fl, sh.nt, al.carve.total);

@@ -57,6 +57,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// non-blocking test of the phase with the given parity
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete; false after kWaitPolls polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   for (uint32_t i = 0; i < kWaitPolls; ++i)
@@ -64,9 +77,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return false;
 }
 
+// A consumer's wait with a caller-chosen bound: polls = 0 is mbar_wait;
+// otherwise at most `polls` non-blocking tests (a plan can shorten the
+// consumers' waits to exercise the timeout path; the drains that make a
+// CTA's shared memory safe to reuse always take the full bound).
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, uint32_t polls) {
+  if (polls == 0) return mbar_wait(bar, parity);
+  for (uint32_t i = 0; i < polls; ++i)
+    if (mbar_test_wait(bar, parity)) return true;
+  return false;
+}
+
 // generic-proxy stores to global memory -> visible to later bulk copies
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// generic-proxy accesses of shared memory ordered before later bulk copies
+// into it (a ring slot read by threads, then refilled by the copy engine)
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 }  // namespace mdhp

@@ -350,6 +350,7 @@ struct XPipe {
   int step_f4;        // float4 per step (NQ * NT)
   int L, S, D, nst;   // steps per pass, steps per stage, buffers, stages per pass
   uint32_t used, issued, base;  // fills consumed (all threads) / issued (thread 0)
+  uint32_t polls;     // bound of a consumer's wait (0: the default)
 };
 
 template <int M>
@@ -382,7 +383,7 @@ __device__ __forceinline__ bool xpass_pipe(int p0, int p1, int i0, XPipe &pp, co
   for (int s = 0; s < pp.nst; ++s) {
     const uint32_t g = pp.used;
     const int slot = (int)(g % (uint32_t)pp.D);
-    if (!mbar_wait(sm.mbar + slot, (g / (uint32_t)pp.D) & 1u)) sm.ctl[3] = 1;
+    if (!mbar_wait_for(sm.mbar + slot, (g / (uint32_t)pp.D) & 1u, pp.polls)) sm.ctl[3] = 1;
     const float4 *buf = sm.ring + (size_t)slot * pp.S * pp.step_f4 + tid;
     const int k0 = s * pp.S, k1 = min(k0 + pp.S, pp.L);
     if (active) {
@@ -410,15 +411,18 @@ __device__ __forceinline__ bool xpass_pipe(int p0, int p1, int i0, XPipe &pp, co
 }
 
 // Waits out the D fills issued and not yet consumed, pp.used .. pp.used + D - 1
-// (bounded): after the last stage of a window, or after a stage whose fill
-// did not arrive in time (that fill included).
+// (each with the full bound, whatever the consumers' bound): after the last
+// stage of a window, or after a stage whose fill did not arrive in time (that
+// fill included).  Returns (uniformly) whether every one of them landed; if
+// not, a copy may still be writing into the ring, which is then not used again.
 template <int M>
-__device__ __forceinline__ void xpipe_drain(XPipe &pp, const Sm<M> &sm) {
+__device__ __forceinline__ bool xpipe_drain(XPipe &pp, const Sm<M> &sm) {
+  bool ok = true;
   for (int d = 0; d < pp.D; ++d) {
     const uint32_t g = pp.used++;
-    mbar_wait(sm.mbar + (g % (uint32_t)pp.D), (g / (uint32_t)pp.D) & 1u);
+    ok &= mbar_wait(sm.mbar + (g % (uint32_t)pp.D), (g / (uint32_t)pp.D) & 1u);
   }
-  __syncthreads();
+  return __syncthreads_and(ok) != 0;
 }
 
 // Event part of the gradient of parameter p (mu_i or alpha_ij): the sum of
@@ -455,7 +459,8 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
   float4 *Xg = XS ? nullptr
                   : a.xbuf + (size_t)(a.slot_base + blockIdx.x) * (M / 4) * (size_t)(xcap + 512);
   constexpr bool pipe = XM == XM_RING;
-  XPipe pp{Xg, (M / 4) * NT, 1, a.pipe_steps, a.pipe_stages, 1, 0u, 0u, 0u};
+  XPipe pp{Xg, (M / 4) * NT, 1, a.pipe_steps, a.pipe_stages, 1, 0u, 0u, 0u, a.wait_polls};
+  bool ring_lost = false;  // a drain gave up: fills may still be landing in the ring
   if (pipe) {
     if (tid == 0) {
       for (int d = 0; d < pp.D; ++d) mbar_init(sm.mbar + d, 1);
@@ -487,7 +492,9 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     const float *tg = a.t + o0;
     const int16_t *ug = a.id + o0;
     const float *wg = a.w ? a.w + o0 : nullptr;
-    int st = (N > xcap) ? (int)kE_ARG : stage_and_validate<M, false>(tg, ug, wg, N, T, Mrt, sm);
+    int st = (pipe && ring_lost) ? (int)kE_TIMEOUT
+             : (N > xcap)        ? (int)kE_ARG
+                                 : stage_and_validate<M, false>(tg, ug, wg, N, T, Mrt, sm);
     if (st != kOK) {
       if (tid == 0) {
         a.status[b] = st;
@@ -553,6 +560,7 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
     const bool use_tol = a.tol > 0.0;
     const float tolf = (float)a.tol;
     int streak = 0, k = 0;
+    bool timed_out = false;
     int wst = a.tol > 0.0 ? kE_MAXITER : kOK;
     float b1t = 1.f, b2t = 1.f;
     // Part2 + Part3 of the current point: computed here for theta_0, then
@@ -571,14 +579,17 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
       if (XS) {
         xpass<M, true, 0>(p0, p1, i0, (const float4 *)sm.xs, xcap, xm, sm, Ls, Lc);
       } else if constexpr (pipe) {
-        if (!xpass_pipe<M>(p0, p1, i0, pp, sm, Ls, Lc)) {  // a fill never arrived
+        if (!xpass_pipe<M>(p0, p1, i0, pp, sm, Ls, Lc)) {  // a fill did not arrive in time
           if (tid == 0) {
             a.status[b] = kE_TIMEOUT;
             a.loglik[b] = __longlong_as_double(0x7ff8000000000000LL);
             a.iters[b] = k;
           }
-          xpipe_drain<M>(pp, sm);
-          return;
+          // the fills in flight land before the CTA goes on; if they do not,
+          // its later windows report the timeout without touching the ring
+          if (!xpipe_drain<M>(pp, sm)) ring_lost = true;
+          timed_out = true;
+          break;
         }
       } else {
         xpass<M, false, NTC>(p0, p1, i0, (const float4 *)Xg, xcap, xm, sm, Ls, Lc);
@@ -663,7 +674,8 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
         break;
       }
     }
-    if (pipe) xpipe_drain<M>(pp, sm);  // the fills issued ahead for an iteration that never ran
+    if (timed_out) continue;  // window reported, ring drained
+    if (pipe && !xpipe_drain<M>(pp, sm)) ring_lost = true;  // fills issued for an iteration that never ran
     for (int p = tid; p < Mrt * Mrt; p += NT)
       a.alpha[(int64_t)b * Mrt * Mrt + p] = sm.alpha[(p / Mrt) * AP + (p % Mrt)];
     for (int i = tid; i < Mrt; i += NT) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];

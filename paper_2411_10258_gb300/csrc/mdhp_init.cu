@@ -32,6 +32,14 @@ namespace mdhp {
 
 constexpr int kBins = 32;
 
+// tensor-core GEMM (mdhp_gemm_tc.cu)
+bool gemm_tc_supported(const void *A, int64_t lda, int a_mn, const void *B, int64_t ldb, int b_mn, int Mm,
+                       int Nn, int Kk);
+mdhp_status gemm_tc(const __nv_bfloat16 *A, int64_t lda, int a_mn, const __nv_bfloat16 *B, int64_t ldb,
+                    int b_mn, int Mm, int Nn, int Kk, const float *bias, int relu, float *Cf,
+                    __nv_bfloat16 *Cb, int64_t ldc, int accumulate, int split, cudaStream_t st);
+int gemm_tc_launches(int Mm, int Nn, int Kk, int accumulate, int split);
+
 __host__ __device__ inline int init_k0(int M) {
   const int K = M + kBins * M * M + 3;
   return (K + 63) / 64 * 64;
@@ -495,6 +503,7 @@ struct mdhp_init_model {
   float *h[4] = {}, *dh[4] = {}, *aux = nullptr, *loss = nullptr;
   __nv_bfloat16 *dhb[4] = {};
   int64_t step = 0;
+  int gemm_engine = 1;  // 0: tensor cores (tcgen05) where the layouts allow; 1: mma.sync
 };
 
 static mdhp_status init_fail(mdhp_status s, const char *msg) {
@@ -504,10 +513,11 @@ static mdhp_status init_fail(mdhp_status s, const char *msg) {
 
 static int grid1(int64_t n, int t = 256) { return (int)((n + t - 1) / t); }
 
-static void launch_gemm(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B,
-                        int64_t sbk, int64_t sbn, int Mm, int Nn, int Kk, const float *bias,
-                        int relu, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, int accumulate,
-                        cudaStream_t st) {
+// The warp-level MMA path (mma.sync), any strides.
+static void launch_gemm_mma(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B,
+                            int64_t sbk, int64_t sbn, int Mm, int Nn, int Kk, const float *bias,
+                            int relu, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, int accumulate,
+                            cudaStream_t st) {
   const int va = (sak == 1 && sam % 8 == 0 && Kk % 8 == 0 && ((uintptr_t)A & 15) == 0) ? 1 : 0;
   const int vb = (sbk == 1 && sbn % 8 == 0 && Kk % 8 == 0 && ((uintptr_t)B & 15) == 0) ? 1 : 0;
   GemmArgs g{A, B, sam, sak, sbk, sbn, Mm, Nn, Kk, bias, relu, accumulate, va, vb, Cf, Cb, ldc};
@@ -522,6 +532,51 @@ static void launch_gemm(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const 
     return;
   }
   k_gemm_bf16<<<grid, 128, 0, st>>>(g);
+}
+
+// Whether a product given by strides (A(m,k) = A[m*sam + k*sak], B(k,n) =
+// B[k*sbk + n*sbn]) runs on the tensor cores (tcgen05): engine 0, one of the
+// two strides of each operand 1, a supported layout, and an FP32 output when
+// the K split needs one.  Fills the major flags and pitches.
+struct TcRoute {
+  bool use;
+  int a_mn, b_mn;
+  int64_t lda, ldb;
+};
+static TcRoute tc_route(int engine, const __nv_bfloat16 *A, int64_t sam, int64_t sak,
+                        const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, int Mm, int Nn, int Kk,
+                        const float *Cf, int accumulate) {
+  TcRoute r{false, 0, 0, 0, 0};
+  if (engine != 0 || !((sak == 1 || sam == 1) && (sbk == 1 || sbn == 1))) return r;
+  r.a_mn = sak == 1 ? 0 : 1;
+  r.b_mn = sbk == 1 ? 0 : 1;
+  r.lda = r.a_mn ? sak : sam;
+  r.ldb = r.b_mn ? sbk : sbn;
+  const bool out_ok = Cf != nullptr || gemm_tc_launches(Mm, Nn, Kk, accumulate, 0) == 1;
+  r.use = out_ok && gemm_tc_supported(A, r.lda, r.a_mn, B, r.ldb, r.b_mn, Mm, Nn, Kk);
+  return r;
+}
+
+// Kernel launches of one product (for the launch counts the library reports).
+static int gemm_launches(int engine, const __nv_bfloat16 *A, int64_t sam, int64_t sak,
+                         const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, int Mm, int Nn, int Kk,
+                         const float *Cf, int accumulate) {
+  const TcRoute r = tc_route(engine, A, sam, sak, B, sbk, sbn, Mm, Nn, Kk, Cf, accumulate);
+  return r.use ? gemm_tc_launches(Mm, Nn, Kk, accumulate, 0) : 1;
+}
+
+// A product on the tensor cores (tcgen05) when tc_route allows it, else on
+// the warp-level MMA path.
+static mdhp_status launch_gemm(int engine, const __nv_bfloat16 *A, int64_t sam, int64_t sak,
+                               const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, int Mm, int Nn, int Kk,
+                               const float *bias, int relu, float *Cf, __nv_bfloat16 *Cb, int64_t ldc,
+                               int accumulate, cudaStream_t st) {
+  const TcRoute r = tc_route(engine, A, sam, sak, B, sbk, sbn, Mm, Nn, Kk, Cf, accumulate);
+  if (r.use)
+    return gemm_tc(A, r.lda, r.a_mn, B, r.ldb, r.b_mn, Mm, Nn, Kk, bias, relu, Cf, Cb, ldc, accumulate,
+                   0, st);
+  launch_gemm_mma(A, sam, sak, B, sbk, sbn, Mm, Nn, Kk, bias, relu, Cf, Cb, ldc, accumulate, st);
+  return MDHP_OK;
 }
 
 extern "C" {
@@ -669,14 +724,29 @@ mdhp_status mdhp_init_features(const mdhp_batch *batch, const float *beta, void 
 }
 
 // Forward over rows [0, Bn) of X (BF16 [Bn][K0]); leaves Y in h[3] (FP32).
-static void init_forward(mdhp_init_model *p, const __nv_bfloat16 *X, int Bn, cudaStream_t st) {
+static mdhp_status init_forward(mdhp_init_model *p, const __nv_bfloat16 *X, int Bn, cudaStream_t st) {
   const __nv_bfloat16 *in = X;
   for (int l = 0; l < 4; ++l) {
     const int din = p->din[l], dout = p->dout[l];
-    launch_gemm(in, din, 1, p->wb + p->off_w[l], 1, din, Bn, dout, din, p->w + p->off_b[l],
-                l < 3 ? 1 : 0, p->h[l], p->hb[l], dout, 0, st);
+    const mdhp_status s = launch_gemm(p->gemm_engine, in, din, 1, p->wb + p->off_w[l], 1, din, Bn, dout,
+                                      din, p->w + p->off_b[l], l < 3 ? 1 : 0, p->h[l], p->hb[l], dout, 0,
+                                      st);
+    if (s != MDHP_OK) return s;
     in = p->hb[l];
   }
+  return MDHP_OK;
+}
+
+// kernel launches of init_forward over Bn rows
+static int init_forward_launches(const mdhp_init_model *p, const __nv_bfloat16 *X, int Bn) {
+  int n = 0;
+  const __nv_bfloat16 *in = X;
+  for (int l = 0; l < 4; ++l) {
+    const int din = p->din[l], dout = p->dout[l];
+    n += gemm_launches(p->gemm_engine, in, din, 1, p->wb + p->off_w[l], 1, din, Bn, dout, din, p->h[l], 0);
+    in = p->hb[l];
+  }
+  return n;
 }
 
 mdhp_status mdhp_init_forward(mdhp_init_model *p, const void *features_bf16, int32_t B, float *out,
@@ -685,7 +755,8 @@ mdhp_status mdhp_init_forward(mdhp_init_model *p, const void *features_bf16, int
   cudaStream_t st = (cudaStream_t)stream;
   for (int b0 = 0; b0 < B; b0 += p->max_batch) {
     const int n = B - b0 < p->max_batch ? B - b0 : p->max_batch;
-    init_forward(p, (const __nv_bfloat16 *)features_bf16 + (size_t)b0 * p->K0, n, st);
+    const mdhp_status s = init_forward(p, (const __nv_bfloat16 *)features_bf16 + (size_t)b0 * p->K0, n, st);
+    if (s != MDHP_OK) return s;
     cudaMemcpyAsync(out + (size_t)b0 * p->O, p->h[3], (size_t)n * p->O * 4, cudaMemcpyDeviceToDevice, st);
   }
   const cudaError_t e = cudaGetLastError();
@@ -696,10 +767,16 @@ mdhp_status mdhp_init_forward(mdhp_init_model *p, const void *features_bf16, int
 }  // extern "C"
 
 namespace mdhp {
-// per chunk of max_batch windows: the features, four GEMMs and the head
+// per chunk of max_batch windows: the features, the four layers' products
+// (one or two launches each) and the head
 int init_predict_launches(const mdhp_init_model *p, int B) {
   if (!p || B <= 0) return 0;
-  return 6 * ((B + p->max_batch - 1) / p->max_batch);
+  int n = 0;
+  for (int b0 = 0; b0 < B; b0 += p->max_batch) {
+    const int rows = B - b0 < p->max_batch ? B - b0 : p->max_batch;
+    n += 2 + init_forward_launches(p, p->X, rows);
+  }
+  return n;
 }
 }  // namespace mdhp
 
@@ -720,7 +797,7 @@ mdhp_status mdhp_init_predict(mdhp_init_model *p, const mdhp_batch *batch, const
     const float *bsub = beta + (int64_t)b0 * bstride;
     mdhp_status s = mdhp_init_features(&sub, bsub, p->X, p->aux, stream);
     if (s != MDHP_OK) return s;
-    init_forward(p, p->X, n, st);
+    if ((s = init_forward(p, p->X, n, st)) != MDHP_OK) return s;
     k_init_head<<<n, 128, 0, st>>>(p->h[3], p->O, p->aux, bsub, bstride, p->M, n,
                                    mu + (int64_t)b0 * p->M, alpha + (int64_t)b0 * p->M * p->M);
   }
@@ -739,7 +816,8 @@ mdhp_status mdhp_init_backward(mdhp_init_model *p, const void *features_bf16,
   if (beta_stride != 1 && beta_stride != p->M) return init_fail(MDHP_E_ARG, "mdhp_init_backward: beta_stride");
   cudaStream_t st = (cudaStream_t)stream;
   const __nv_bfloat16 *X = (const __nv_bfloat16 *)features_bf16;
-  init_forward(p, X, B, st);
+  mdhp_status s = init_forward(p, X, B, st);
+  if (s != MDHP_OK) return s;
   cudaMemsetAsync(p->loss, 0, 4, st);
   cudaMemsetAsync(p->g, 0, p->nparams * 4, st);
   k_init_loss<<<B, 128, 0, st>>>(p->h[3], p->O, mu_cold, beta, beta_stride, p->M, B, mu_target,
@@ -748,13 +826,15 @@ mdhp_status mdhp_init_backward(mdhp_init_model *p, const void *features_bf16,
     const int din = p->din[l], dout = p->dout[l];
     const __nv_bfloat16 *in = l > 0 ? p->hb[l - 1] : X;
     // dW[dout][din] = dY^T [dout][B] x In [B][din]
-    launch_gemm(p->dhb[l], 1, dout, in, din, 1, dout, din, B, nullptr, 0, p->g + p->off_w[l], nullptr,
-                din, 1, st);
+    if ((s = launch_gemm(p->gemm_engine, p->dhb[l], 1, dout, in, din, 1, dout, din, B, nullptr, 0,
+                         p->g + p->off_w[l], nullptr, din, 1, st)) != MDHP_OK)
+      return s;
     k_bias_grad<<<grid1(dout), 256, 0, st>>>(p->dh[l], B, dout, p->g + p->off_b[l]);
     if (l > 0) {
       // dIn[B][din] = dY [B][dout] x W [dout][din]; then the ReLU of layer l-1
-      launch_gemm(p->dhb[l], dout, 1, p->wb + p->off_w[l], din, 1, B, din, dout, nullptr, 0,
-                  p->dh[l - 1], nullptr, din, 0, st);
+      if ((s = launch_gemm(p->gemm_engine, p->dhb[l], dout, 1, p->wb + p->off_w[l], din, 1, B, din, dout,
+                           nullptr, 0, p->dh[l - 1], nullptr, din, 0, st)) != MDHP_OK)
+        return s;
       const int64_t n = (int64_t)B * din;
       k_relu_bwd<<<grid1(n), 256, 0, st>>>(p->dh[l - 1], p->h[l - 1], p->dhb[l - 1], n);
     }
@@ -794,6 +874,37 @@ mdhp_status mdhp_init_train_step(mdhp_init_model *p, const void *features_bf16,
                                            alpha_target, B, loss_out, stream);
   if (s != MDHP_OK) return s;
   return mdhp_init_apply(p, lr, weight_decay, stream);
+}
+
+mdhp_status mdhp_init_model_set_gemm(mdhp_init_model *p, int32_t engine) {
+  if (!p || engine < 0 || engine > 1) return init_fail(MDHP_E_ARG, "mdhp_init_model_set_gemm: bad argument");
+  p->gemm_engine = engine;
+  return MDHP_OK;
+}
+
+mdhp_status mdhp_gemm_bf16(const void *A, int64_t lda, int32_t a_mn, const void *B, int64_t ldb,
+                           int32_t b_mn, int32_t M, int32_t N, int32_t K, const float *bias,
+                           int32_t relu, float *C, void *C_bf16, int64_t ldc, int32_t accumulate,
+                           int32_t engine, void *stream) {
+  if (!A || !B || M < 1 || N < 1 || K < 1 || engine < 0 || engine > 1 || (!C && (accumulate || !C_bf16)))
+    return init_fail(MDHP_E_ARG, "mdhp_gemm_bf16: bad argument");
+  const __nv_bfloat16 *a = (const __nv_bfloat16 *)A, *b = (const __nv_bfloat16 *)B;
+  __nv_bfloat16 *cb = accumulate ? nullptr : (__nv_bfloat16 *)C_bf16;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (engine == 0) {
+    if (!gemm_tc_supported(A, lda, a_mn, B, ldb, b_mn, M, N, K))
+      return init_fail(MDHP_E_UNSUPPORTED, "mdhp_gemm_bf16: layout not supported by the tensor-core GEMM");
+    if (!C && gemm_tc_launches(M, N, K, accumulate, 0) > 1)
+      return init_fail(MDHP_E_ARG, "mdhp_gemm_bf16: this shape splits K and needs the FP32 output");
+    return gemm_tc(a, lda, a_mn, b, ldb, b_mn, M, N, K, bias, relu, C, cb, ldc, accumulate, 0, st);
+  }
+  const int64_t sam = a_mn ? 1 : lda, sak = a_mn ? lda : 1;
+  const int64_t sbk = b_mn ? ldb : 1, sbn = b_mn ? 1 : ldb;
+  launch_gemm_mma(a, sam, sak, b, sbk, sbn, M, N, K, accumulate ? nullptr : bias, accumulate ? 0 : relu, C,
+                  cb, ldc, accumulate, st);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
+  return MDHP_OK;
 }
 
 }  // extern "C"

@@ -49,6 +49,14 @@ struct FitArgs {
   int qdir;
   int *dq;
   int slot_base;  // first feature-scratch slot of this launch
+  // recursion fit, streamed events: 1 = pass 2 reads them through the
+  // bulk-copy ring (batch arrays 16-byte aligned, no weights); n_total =
+  // events in the batch arrays (the copies are clamped to them)
+  int ring;
+  int64_t n_total;
+  // bulk-copy rings (features, events): polls of a consumer's wait, 0 = the
+  // default bound (kWaitPolls suspending polls)
+  uint32_t wait_polls;
   Carve carve;
 };
 
@@ -175,9 +183,21 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
   const int np = Mrt + Mrt * Mrt + nb;
   const int nupd = a.fit_beta ? np : Mrt + Mrt * Mrt;
   const int tid = threadIdx.x;
-  // theta_{k-1} (restored after a non-finite evaluation): the CTA's device
-  // slot when the launch provides one, else shared memory
-  float *prevp = a.pbuf ? a.pbuf + (size_t)blockIdx.x * a.pstride : sm.prev;
+  // theta_{k-1} (restored after a non-finite evaluation), the gradient
+  // buffer and the Adam moments: the CTA's device slot (four blocks of
+  // pstride / 4 floats) when the launch provides one, else shared memory
+  float *slotp = a.pbuf ? a.pbuf + (size_t)blockIdx.x * a.pstride : nullptr;
+  const int pq = a.pstride / 4;
+  float *prevp = slotp ? slotp : sm.prev;
+  float *gbp = slotp ? slotp + pq : sm.gbuf;
+  float *amp = slotp ? slotp + 2 * pq : sm.am;
+  float *avp = slotp ? slotp + 3 * pq : sm.av;
+  if (a.optimizer == 1) {
+    for (int p = tid; p < np; p += blockDim.x) {
+      amp[p] = 0.f;
+      avp[p] = 0.f;
+    }
+  }
   constexpr bool FIXED = std::is_same<EV, EvS>::value && !LEARN && BM == 0;
   setup_chunks(a.NC, N, T, ev, sm.bnd, sm.anc);
   if (!LEARN) prepare_states<M, SPL, BM, false>(a.NC, ev, Mrt, sm);
@@ -213,7 +233,7 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
     for (int p = tid; p < np; p += blockDim.x) {
       const float g = grad_of<M, SPL, BM, LEARN>(p, Mrt, T, sm);
       bad |= !isfinite(g);
-      sm.gbuf[p] = g;
+      gbp[p] = g;
     }
     bad = __syncthreads_or(bad);
     if (bad) {
@@ -228,14 +248,14 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
     b1t *= a.b1;
     b2t *= a.b2;
     for (int p = tid; p < nupd; p += blockDim.x) {
-      const float g = sm.gbuf[p] * invN;
+      const float g = gbp[p] * invN;
       float &th = param_ref<M>(p, Mrt, sm);
       float step;
       if (a.optimizer == 1) {
-        const float m1 = a.b1 * sm.am[p] + (1.f - a.b1) * g;
-        const float m2 = a.b2 * sm.av[p] + (1.f - a.b2) * g * g;
-        sm.am[p] = m1;
-        sm.av[p] = m2;
+        const float m1 = a.b1 * amp[p] + (1.f - a.b1) * g;
+        const float m2 = a.b2 * avp[p] + (1.f - a.b2) * g * g;
+        amp[p] = m1;
+        avp[p] = m2;
         const float mh = m1 / (1.f - b1t), vh = m2 / (1.f - b2t);
         step = a.lr * mh / (sqrtf(vh) + a.eps);
       } else {
@@ -275,6 +295,15 @@ __global__ void __launch_bounds__(256, 2) k_fit(FitArgs a) {
   const int nb = BM == 0 ? 1 : Mrt;
   const int np = Mrt + Mrt * Mrt + nb;
   const int tid = threadIdx.x;
+  if (!STAGE && a.ring) {  // the streamed events' ring: one mbarrier per chunk and stage
+    if (tid == 0) {
+      for (int q = 0; q < a.NC * kRingD; ++q) mbar_init(sm.rbar + q, 1);
+      mbar_init_fence();
+      sm.ctl[4] = 0;
+    }
+    for (int c = tid; c < a.NC; c += blockDim.x) sm.rfill[c] = 0;
+    __syncthreads();
+  }
   for (;;) {
     if (tid == 0) sm.ctl[1] = atomicAdd(a.queue, 1);
     __syncthreads();
@@ -317,15 +346,13 @@ __global__ void __launch_bounds__(256, 2) k_fit(FitArgs a) {
       for (int i = tid; i < Mrt; i += blockDim.x)
         sm.mu[i] = 0.5f * (float)max(sm.cnt[i], 1) / T;
     }
-    if (a.optimizer == 1) {
-      for (int p = tid; p < np; p += blockDim.x) {
-        sm.am[p] = 0.f;
-        sm.av[p] = 0.f;
-      }
-    }
     __syncthreads();
     if (STAGE) {
       const EvS ev{sm.ev_t, sm.ev_u, wg ? sm.ev_w : nullptr};
+      fit_window<M, SPL, BM, LEARN>(a, b, N, T, ev, sm);
+    } else if (a.ring) {
+      const EvRing ev{tg, ug, nullptr, a.t, a.id, o0, a.n_total, sm.rt, sm.ru, sm.rbar, sm.rfill,
+                      sm.ctl + 4, a.wait_polls};
       fit_window<M, SPL, BM, LEARN>(a, b, N, T, ev, sm);
     } else {
       const EvG ev{tg, ug, wg};

@@ -38,6 +38,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mdhp_async.cuh"
+
 namespace mdhp {
 
 constexpr float kLog2e = 1.4426950408889634f;
@@ -54,16 +56,10 @@ struct UsePriv {
   static constexpr bool value = M <= 32;
 };
 
-// 2^x for the decay factors of the recursion.  x = k + f with k = rint(x) and
-// |f| <= 1/2; 2^f from its Taylor series e^(f ln 2) to degree 7 (truncation
+// 2^f for |f| <= 1/2: Taylor series of e^(f ln 2) to degree 7 (truncation
 // below 6e-9 relative), evaluated by Horner so the last rounding is a plain
-// round-to-nearest; 2^k applied exactly through the exponent field.  Unlike
-// the approximate hardware exponential its error has no one-sided bias, which
-// matters because the recursion multiplies thousands of these factors.
-__device__ __forceinline__ float exp2_acc(float x) {
-  const float xc = fmaxf(x, -125.f);
-  const float k = rintf(xc);
-  const float f = xc - k;
+// round-to-nearest.
+__device__ __forceinline__ float exp2_poly(float f) {
   float p = 1.5252733804059840e-05f;
   p = fmaf(p, f, 1.5403530393381608e-04f);
   p = fmaf(p, f, 1.3333558146428443e-03f);
@@ -71,9 +67,29 @@ __device__ __forceinline__ float exp2_acc(float x) {
   p = fmaf(p, f, 5.5504108664821580e-02f);
   p = fmaf(p, f, 2.4022650695910071e-01f);
   p = fmaf(p, f, 6.9314718055994531e-01f);
-  p = fmaf(p, f, 1.0f);
-  const float r = p * __int_as_float(((int)k + 127) << 23);
-  return x < -125.f ? 0.f : r;
+  return fmaf(p, f, 1.0f);
+}
+// 2^x for the decay factors of the recursion.  x = k + f with k the nearest
+// integer to x and |f| <= 1/2; 2^f from exp2_poly; 2^k applied exactly by
+// adding k to the exponent field.  Unlike the approximate hardware
+// exponential its error has no one-sided bias, which matters because the
+// recursion multiplies thousands of these factors.
+//
+// The rounding to k adds 1.5 * 2^23 (where the float spacing is 1, so the sum
+// is rounded to an integer, half to even) and subtracts it again: f is then
+// exact, and k sits in the low bits of the sum, two's complement, so that
+// shifting the sum's bit pattern left by 23 gives k << 23.  Everything runs on
+// the FMA and integer pipes (no float-to-int conversion, no multiply by 2^k).
+// Arguments below -125 are taken as -125: the factor is then 2^-125 instead
+// of the exact value below it, a difference no recursion state can resolve
+// against intensities of at least mu_floor.  Callers keep x <= 64.
+__device__ __forceinline__ float exp2_acc(float x) {
+  constexpr float kRound = 12582912.f;  // 1.5 * 2^23
+  const float xc = fmaxf(x, -125.f);
+  const float kt = xc + kRound;
+  const float f = xc - (kt - kRound);
+  const float p = exp2_poly(f);
+  return __int_as_float(__float_as_int(p) + (__float_as_int(kt) << 23));
 }
 
 // Hardware base-2 logarithm and reciprocal of an intensity (PTX lg2.approx /
@@ -149,6 +165,10 @@ struct EvS {
   __device__ __forceinline__ float time(int n) const { return t[n]; }
   __device__ __forceinline__ int id(int n) const { return (int)u[n]; }
   __device__ __forceinline__ float wt(int n) const { return w ? w[n] : 1.f; }
+  // a chunk's events in order (pass 2): nothing to stage
+  __device__ __forceinline__ void chunk_begin(int, int, int, int, unsigned) const {}
+  __device__ __forceinline__ void next(int n, float &tt, int &uu) const { get(n, tt, uu); }
+  __device__ __forceinline__ void chunk_end() const {}
 };
 
 struct EvG {
@@ -162,6 +182,141 @@ struct EvG {
   __device__ __forceinline__ float time(int n) const { return __ldg(t + n); }
   __device__ __forceinline__ int id(int n) const { return (int)__ldg(u + n); }
   __device__ __forceinline__ float wt(int n) const { return w ? __ldg(w + n) : 1.f; }
+  __device__ __forceinline__ void chunk_begin(int, int, int, int, unsigned) const {}
+  __device__ __forceinline__ void next(int n, float &tt, int &uu) const { get(n, tt, uu); }
+  __device__ __forceinline__ void chunk_end() const {}
+};
+
+// Streamed events of a window too long to stage whole, delivered to pass 2
+// through a ring of shared-memory stages per chunk, each stage filled by bulk
+// copies (the TMA engine's linear mode, CTA-local, no multicast) of the
+// chunk's next kRingK times and ids, completed on the stage's mbarrier.  The
+// chunk's first thread (source slice 0) issues the copies kRingD stages ahead;
+// all SPL threads of the chunk wait (bounded) on a stage before reading it.
+// A copy must start on a 16-byte boundary and move a multiple of 16 bytes, so
+// a stage copies the 16-byte-aligned span around its events, clamped to the
+// batch arrays; events past the clamp (the batch's last few) and the tie
+// groups that reach back into an earlier stage are read from global memory.
+// A wait that gives up sets the CTA's flag, and the ring is not used again
+// by that CTA: its chunks read global memory from then on (same results).
+// Random access (chunk boundaries, pass 1) reads global memory directly.
+constexpr int kRingK = 128, kRingD = 2;
+constexpr int kRingKT = kRingK + 8;   // time slots per stage (alignment slack)
+constexpr int kRingKU = kRingK + 16;  // id slots per stage
+__host__ __device__ inline int ring_bytes(int NC) {
+  return NC * kRingD * (kRingKT * 4 + kRingKU * 2 + 8);
+}
+
+struct EvRing {
+  const float *t;      // window's events (global)
+  const int16_t *u;
+  const float *w;      // always nullptr: weighted windows do not use the ring
+  const float *tb;     // batch arrays (16-byte aligned)
+  const int16_t *ub;
+  int64_t o0, ntot;    // window's first event in the batch; events in the batch
+  float *rt;           // [NC][kRingD][kRingKT]
+  uint16_t *ru;        // [NC][kRingD][kRingKU]
+  uint64_t *bar;       // [NC][kRingD]
+  int *fillc;          // [NC] stages each chunk has consumed (persists across windows)
+  int *dead;           // a wait gave up: the ring is off for this CTA
+  uint32_t polls;      // bound of a stage wait (0: the default)
+  // current chunk (set by chunk_begin, advanced by next)
+  mutable int c, s, b0, b1, nst, g, f0;
+  mutable int64_t S0, S1, U0, U1;
+  mutable unsigned gm;
+  mutable bool on;
+
+  __device__ __forceinline__ void get(int n, float &tt, int &uu) const {
+    tt = __ldg(t + n);
+    uu = (int)__ldg(u + n);
+  }
+  __device__ __forceinline__ float time(int n) const { return __ldg(t + n); }
+  __device__ __forceinline__ int id(int n) const { return (int)__ldg(u + n); }
+  __device__ __forceinline__ float wt(int) const { return 1.f; }
+
+  __device__ __forceinline__ int slot(int gg) const { return (f0 + gg) % kRingD; }
+  __device__ __forceinline__ uint32_t parity(int gg) const { return (uint32_t)(((f0 + gg) / kRingD) & 1); }
+  // aligned spans of stage gg (absolute batch indices), clamped to the arrays
+  __device__ __forceinline__ void span(int gg, int64_t &s0, int64_t &s1, int64_t &u0, int64_t &u1) const {
+    const int e0 = b0 + gg * kRingK, e1 = min(e0 + kRingK, b1);
+    const int64_t a0 = o0 + e0, a1 = o0 + e1;
+    s0 = a0 & ~(int64_t)3;
+    s1 = (a1 + 3) & ~(int64_t)3;
+    const int64_t lt = ntot & ~(int64_t)3;
+    if (s1 > lt) s1 = lt > s0 ? lt : s0;
+    u0 = a0 & ~(int64_t)7;
+    u1 = (a1 + 7) & ~(int64_t)7;
+    const int64_t lu = ntot & ~(int64_t)7;
+    if (u1 > lu) u1 = lu > u0 ? lu : u0;
+  }
+  __device__ __forceinline__ void issue(int gg) const {
+    int64_t s0, s1, u0, u1;
+    span(gg, s0, s1, u0, u1);
+    const int sl = slot(gg);
+    uint64_t *br = bar + c * kRingD + sl;
+    const uint32_t bt = (uint32_t)(s1 - s0) * 4u, bu = (uint32_t)(u1 - u0) * 2u;
+    fence_proxy_async_shared();  // the slot's earlier reads before the copy's writes
+    mbar_expect_tx(br, bt + bu);
+    if (bt) bulk_copy_g2s(rt + (c * kRingD + sl) * kRingKT, tb + s0, bt, br);
+    if (bu) bulk_copy_g2s(ru + (c * kRingD + sl) * kRingKU, ub + u0, bu, br);
+  }
+  // wait for stage gg (every thread of the chunk; the outcome is made uniform)
+  __device__ __forceinline__ void enter(int gg) const {
+    const bool ok = __all_sync(gm, mbar_wait_for(bar + c * kRingD + slot(gg), parity(gg), polls));
+    g = gg;
+    if (!ok) {
+      if (s == 0) *dead = 1;
+      on = false;
+      return;
+    }
+    span(gg, S0, S1, U0, U1);
+  }
+  __device__ __forceinline__ void chunk_begin(int cc, int ss, int bb0, int bb1, unsigned mask) const {
+    c = cc;
+    s = ss;
+    b0 = bb0;
+    b1 = bb1;
+    gm = mask;
+    g = 0;
+    const int lead = __ffs(mask) - 1;
+    const int off = __shfl_sync(mask, *dead, lead);  // one reading for the whole chunk
+    f0 = __shfl_sync(mask, fillc[cc], lead);
+    nst = off ? 0 : (bb1 - bb0 + kRingK - 1) / kRingK;
+    on = nst > 0;
+    if (!on) return;
+    if (s == 0)
+      for (int gg = 0; gg < kRingD && gg < nst; ++gg) issue(gg);
+    enter(0);
+  }
+  __device__ __forceinline__ void next(int n, float &tt, int &uu) const {
+    if (on) {
+      const int gn = (n - b0) / kRingK;
+      if (gn != g) {  // the chunk's threads are done with stage g: refill its slot
+        __syncwarp(gm);
+        if (s == 0 && g + kRingD < nst) issue(g + kRingD);
+        enter(gn);
+      }
+    }
+    if (on) {
+      const int64_t a = o0 + n;
+      const int sl = slot(g);
+      tt = a < S1 ? rt[(c * kRingD + sl) * kRingKT + (int)(a - S0)] : __ldg(t + n);
+      uu = a < U1 ? (int)ru[(c * kRingD + sl) * kRingKU + (int)(a - U0)] : (int)__ldg(u + n);
+    } else {
+      get(n, tt, uu);
+    }
+  }
+  // Every stage was issued and entered by the end of a chunk, unless a wait
+  // gave up at stage g: then stages g .. g + kRingD - 1 (those issued) are
+  // waited out here, bounded, before the chunk's threads go on.
+  __device__ __forceinline__ void chunk_end() const {
+    if (nst > 0 && !on) {
+      for (int gg = g; gg < nst && gg < g + kRingD; ++gg)
+        mbar_wait(bar + c * kRingD + slot(gg), parity(gg));
+    }
+    __syncwarp(gm);
+    if (s == 0) fillc[c] = f0 + nst;
+  }
 };
 
 // First event of chunk c out of NC over [0, N): the even split moved forward
@@ -180,16 +335,25 @@ __device__ __forceinline__ int chunk_begin(int c, int NC, int N, const EV &ev) {
 struct Carve {
   // byte offsets
   int alpha, oh, ga, mu, gm, beta, bl2, gb, W, cnt, C, dC, endR, endS, anc, bnd, encR, encS, prev,
-      gbuf, am, av, red, ctl, gpriv, mpriv, ev_t, ev_u, ev_w, tstart, tf, tl, P, xs, ring, mbar;
+      gbuf, am, av, red, ctl, gpriv, mpriv, ev_t, ev_u, ev_w, tstart, tf, tl, P, xs, ring, mbar,
+      rt, ru, rbar, rfill;  // streamed events' bulk-copy ring (recursion fit)
   int total;
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 __host__ __device__ inline int pitch4(int M) { return M + 4; }  // 16-byte rows, staggered banks
+// Shared d/dalpha copy (M = 64, updated with shared atomics): one pad word
+// after every 8 columns and an odd row pitch, so that the 8 threads of a
+// chunk (8 consecutive sources each) hit 8 different banks for any target row.
+__host__ __device__ inline int ga_pitch(int M) { return M + M / 8 + 1; }
+__host__ __device__ inline int ga_col(int j) { return j + (j >> 3); }
 
+// prev_smem = false: theta_{k-1}, the gradient buffer and the Adam moments
+// live in the launch's per-CTA device slot instead of shared memory.
+// ring: the streamed events' bulk-copy ring (ring_bytes(NC)).
 __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, bool weights,
                                             bool learn, bool adam, bool fit, bool priv,
-                                            bool prev_smem = true) {
+                                            bool prev_smem = true, bool ring = false) {
   const int NC = NT / SPL;
   Carve c = {};
   int o = 0;
@@ -199,7 +363,7 @@ __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, 
   c.red = take(32 * 8);
   c.ctl = take(16 * 4);
   c.alpha = take(M * AP * 4);
-  c.ga = priv ? 0 : take(M * (M + 1) * 4);
+  c.ga = priv ? 0 : take(M * ga_pitch(M) * 4);
   c.mu = take(M * 4);
   c.gm = take(M * 4);
   c.beta = take(M * 4);
@@ -216,14 +380,20 @@ __host__ __device__ inline Carve make_carve(int M, int NT, int SPL, int ev_cap, 
   c.encR = take(NC * M * 4);
   c.encS = learn ? take(NC * M * 4) : c.encR;
   c.prev = (fit && prev_smem) ? take(npm * 4) : 0;  // else in the launch's per-CTA device slot
-  c.gbuf = fit ? take(npm * 4) : 0;
-  c.am = (fit && adam) ? take(npm * 4) : 0;
-  c.av = (fit && adam) ? take(npm * 4) : 0;
+  c.gbuf = (fit && prev_smem) ? take(npm * 4) : 0;
+  c.am = (fit && adam && prev_smem) ? take(npm * 4) : 0;
+  c.av = (fit && adam && prev_smem) ? take(npm * 4) : 0;
   c.gpriv = priv ? take(M * (M / SPL) * NT * 4) : 0;  // [id][slice][thread] float4
   c.mpriv = priv ? take(M * NC * 4) : 0;                // [id][chunk]
   c.ev_t = ev_cap > 0 ? take(ev_cap * 4) : 0;
   c.ev_w = (ev_cap > 0 && weights) ? take(ev_cap * 4) : 0;
   c.ev_u = ev_cap > 0 ? take(ev_cap * 2) : 0;
+  if (ring && ev_cap == 0) {
+    c.rt = take(NC * kRingD * kRingKT * 4);
+    c.ru = take(NC * kRingD * kRingKU * 2);
+    c.rbar = take(NC * kRingD * 8);
+    c.rfill = take(NC * 4);
+  }
   c.total = o;
   return c;
 }
@@ -287,6 +457,10 @@ struct Sm {
   float *P;
   float4 *xs, *ring;
   uint64_t *mbar;
+  float *rt;         // streamed events' ring: times [NC][kRingD][kRingKT]
+  uint16_t *ru;      //   ids [NC][kRingD][kRingKU]
+  uint64_t *rbar;    //   one mbarrier per chunk and stage
+  int *rfill;        //   stages consumed per chunk
   double *red;
   float *ev_t, *ev_w;
   uint16_t *ev_u;
@@ -307,6 +481,8 @@ struct Sm {
     tstart = (int *)(base + c.tstart); tf = (int *)(base + c.tf); tl = (int *)(base + c.tl);
     P = (float *)(base + c.P); xs = (float4 *)(base + c.xs);
     ring = (float4 *)(base + c.ring); mbar = (uint64_t *)(base + c.mbar);
+    rt = (float *)(base + c.rt); ru = (uint16_t *)(base + c.ru);
+    rbar = (uint64_t *)(base + c.rbar); rfill = (int *)(base + c.rfill);
   }
 };
 
@@ -333,10 +509,15 @@ struct Walker {
   float R[MS];
   float S[LEARN ? MS : 1];
   float b2[BM == 0 ? 1 : MS];  // beta * log2(e)
+  float bmax;                   // the largest of b2
 
   __device__ __forceinline__ void load_beta(const float *bl2, int base) {
+    bmax = 0.f;
 #pragma unroll
-    for (int jj = 0; jj < (BM == 0 ? 1 : MS); ++jj) b2[jj] = bl2[BM == 0 ? 0 : base + jj];
+    for (int jj = 0; jj < (BM == 0 ? 1 : MS); ++jj) {
+      b2[jj] = bl2[BM == 0 ? 0 : base + jj];
+      bmax = fmaxf(bmax, b2[jj]);
+    }
   }
   __device__ __forceinline__ void zero() {
 #pragma unroll
@@ -350,6 +531,15 @@ struct Walker {
       const float a = exp2_acc(-b2[0] * dt);
 #pragma unroll
       for (int jj = 0; jj < MS; ++jj) {
+        if (LEARN) S[jj] = a * fmaf(dt, R[jj], S[jj]);
+        R[jj] *= a;
+      }
+    } else if (bmax * dt <= 0.5f) {
+      // every exponent in [-1/2, 0]: exp2_acc reduces to its polynomial
+      // (k = 0, f = x), so the same factors come without the range reduction
+#pragma unroll
+      for (int jj = 0; jj < MS; ++jj) {
+        const float a = exp2_poly(-b2[BM == 0 ? 0 : jj] * dt);
         if (LEARN) S[jj] = a * fmaf(dt, R[jj], S[jj]);
         R[jj] *= a;
       }
@@ -412,6 +602,30 @@ __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float 
     }
     return;
   }
+  if constexpr (!UsePriv<M>::value) {
+    // the d/dalpha sums of this capacity already meet in shared atomics, so
+    // the run-to-run order of the sums is not fixed anyway: the chunk's SPL
+    // threads take every SPL-th event each and add its contribution to the
+    // chunk's state with shared atomics (one exponential per event in all,
+    // instead of a walk of every event by every thread of the chunk)
+    const unsigned gmask =
+        (SPL >= 32) ? 0xffffffffu : (((1u << SPL) - 1u) << ((threadIdx.x & 31) & ~(SPL - 1)));
+#pragma unroll
+    for (int jj = 0; jj < MS; ++jj) {
+      sm.encR[c * M + base + jj] = 0.f;
+      if (LEARN) sm.encS[c * M + base + jj] = 0.f;
+    }
+    __syncwarp(gmask);
+    for (int n = b0 + s; n < b1; n += SPL) {
+      const int u = ev.id(n);
+      const float d = a1 - ev.time(n);
+      const float we = ev.wt(n) * exp2_acc(-sm.bl2[BM == 0 ? 0 : u] * d);
+      atomicAdd(&sm.encR[c * M + u], we);
+      if (LEARN) atomicAdd(&sm.encS[c * M + u], we * d);
+    }
+    __syncwarp(gmask);
+    return;
+  }
   float R[MS], S[LEARN ? MS : 1];
 #pragma unroll
   for (int jj = 0; jj < MS; ++jj) {
@@ -439,26 +653,69 @@ __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float 
   }
 }
 
-// Per-source scan over chunks: encR/encS[c] become entering states; end state
-// (at T_span, all events included) goes to endR/endS.  Threads j < M.
+// Per-source scan over chunks: encR/encS[c] become entering states; the end
+// state (at T_span, all events included) goes to endR/endS.
+//
+// The effect of chunk c on source j's state is the affine map
+//   R -> A_c R + r_c,   S -> A_c (S + D_c R) + s_c,   A_c = exp(-beta_j D_c),
+// D_c the chunk's length in time and (r_c, s_c) its own contribution (pass 1).
+// Such maps compose associatively (g after f):
+//   A = A_g A_f,  D = D_f + D_g,  r = A_g r_f + r_g,  s = A_g (s_f + D_g r_f) + s_g,
+// so every chunk's entering state is an exclusive scan of the maps applied to
+// the zero state.  It runs as a warp-level scan: warp w takes sources w,
+// w + (warps), ...; lane l first composes its ceil(NC / 32) consecutive chunks,
+// the warp scans the 32 lane aggregates with shuffles (five steps), and each
+// lane then walks its own chunks from its exclusive prefix.
 template <int M, int BM, bool LEARN>
 __device__ __forceinline__ void scan_chunks(int NC, const Sm<M> &sm) {
-  const int j = threadIdx.x;
-  if (j >= M) return;
-  const float b = sm.bl2[BM == 0 ? 0 : j];
-  float R = 0.f, S = 0.f;
-  for (int c = 0; c < NC; ++c) {
-    const float lr = sm.encR[c * M + j];
-    const float ls = LEARN ? sm.encS[c * M + j] : 0.f;
-    sm.encR[c * M + j] = R;
-    if (LEARN) sm.encS[c * M + j] = S;
-    const float D = sm.anc[c + 1] - sm.anc[c];
-    const float A = exp2_acc(-b * D);
-    if (LEARN) S = fmaf(A, fmaf(D, R, S), ls);
-    R = fmaf(A, R, lr);
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int G = (NC + 31) >> 5;
+  const int c0 = min(lane * G, NC), c1 = min(c0 + G, NC);
+  for (int j = threadIdx.x >> 5; j < M; j += nw) {
+    const float b = sm.bl2[BM == 0 ? 0 : j];
+    float A = 1.f, D = 0.f, r = 0.f, s = 0.f;  // this lane's chunks, composed
+    for (int c = c0; c < c1; ++c) {
+      const float Dc = sm.anc[c + 1] - sm.anc[c];
+      const float Ac = exp2_acc(-b * Dc);
+      if (LEARN) s = fmaf(Ac, fmaf(Dc, r, s), sm.encS[c * M + j]);
+      r = fmaf(Ac, r, sm.encR[c * M + j]);
+      A *= Ac;
+      D += Dc;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {  // inclusive scan: earlier lanes' maps first
+      const float Ap = __shfl_up_sync(0xffffffffu, A, o);
+      const float Dp = __shfl_up_sync(0xffffffffu, D, o);
+      const float rp = __shfl_up_sync(0xffffffffu, r, o);
+      const float sp = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) {
+        if (LEARN) s = fmaf(A, fmaf(D, rp, sp), s);
+        r = fmaf(A, rp, r);
+        A *= Ap;
+        D += Dp;
+      }
+    }
+    float R = __shfl_up_sync(0xffffffffu, r, 1);  // state entering this lane's first chunk
+    float S = __shfl_up_sync(0xffffffffu, s, 1);
+    if (lane == 0) {
+      R = 0.f;
+      S = 0.f;
+    }
+    for (int c = c0; c < c1; ++c) {
+      const float Dc = sm.anc[c + 1] - sm.anc[c];
+      const float Ac = exp2_acc(-b * Dc);
+      const float lr = sm.encR[c * M + j];
+      const float ls = LEARN ? sm.encS[c * M + j] : 0.f;
+      sm.encR[c * M + j] = R;
+      if (LEARN) sm.encS[c * M + j] = S;
+      if (LEARN) S = fmaf(Ac, fmaf(Dc, R, S), ls);
+      R = fmaf(Ac, R, lr);
+    }
+    if (lane == 31) {  // every chunk composed: the state at T_span
+      sm.endR[j] = r;
+      if (LEARN) sm.endS[j] = s;
+    }
   }
-  sm.endR[j] = R;
-  if (LEARN) sm.endS[j] = S;
 }
 
 // Pass 2 for chunk c: lnL (log2 units, Kahan), d/dmu, d/dalpha, d/dbeta.
@@ -483,6 +740,7 @@ __device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float 
     if (LEARN) wk.S[jj] = sm.encS[c * M + base + jj];
   }
   float4 *gp = reinterpret_cast<float4 *>(sm.gpriv);
+  ev.chunk_begin(c, s, b0, b1, gmask);  // streamed events: start this chunk's copies
   float tprev = a0;
   int gs = b0;
   int pu = 0;
@@ -490,7 +748,7 @@ __device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float 
   for (int n = b0; n < b1; ++n) {
     float tn;
     int un;
-    ev.get(n, tn, un);
+    ev.next(n, tn, un);
     if (tn > tprev) {
       if (n - gs == 1) {
         wk.add(pu - base, pw);
@@ -537,9 +795,9 @@ __device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float 
         g[q * NT] = x;
       }
     } else {
-      float *grow = sm.ga + un * (M + 1) + base;
+      float *grow = sm.ga + un * ga_pitch(M);
 #pragma unroll
-      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[jj], r * wk.R[jj]);
+      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[ga_col(base + jj)], r * wk.R[jj]);
     }
     if (LEARN) {
 #pragma unroll
@@ -551,6 +809,7 @@ __device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float 
       }
     }
   }
+  ev.chunk_end();
 }
 
 // ---------------------------------------------------------------------------
@@ -661,7 +920,7 @@ __device__ __forceinline__ void clear_accumulators(Sm<M> &sm) {
     }
     for (int p = tid; p < M * (NT / SPL); p += NT) sm.mpriv[p] = 0.f;
   } else {
-    for (int p = tid; p < M * (M + 1); p += NT) sm.ga[p] = 0.f;
+    for (int p = tid; p < M * ga_pitch(M); p += NT) sm.ga[p] = 0.f;
     for (int j = tid; j < M; j += NT) sm.gm[j] = 0.f;
   }
   for (int j = tid; j < M; j += NT) sm.gb[j] = 0.f;
@@ -762,9 +1021,9 @@ __device__ __forceinline__ void pass2_fixed(int c, int s, int b0, int b1, const 
         g[q * NT] = x;
       }
     } else {
-      float *grow = sm.ga + un * (M + 1) + base;
+      float *grow = sm.ga + un * ga_pitch(M);
 #pragma unroll
-      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[jj], r * wk.R[jj]);
+      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[ga_col(base + jj)], r * wk.R[jj]);
     }
   }
 }
@@ -882,7 +1141,7 @@ __device__ __forceinline__ float alpha_event_sum(int i, int j, const Sm<M> &sm) 
     for (int c = 0; c < NC; ++c) acc += base[(c * SPL + s) * 4];
     return acc;
   }
-  return sm.ga[i * (M + 1) + j];
+  return sm.ga[i * ga_pitch(M) + ga_col(j)];
 }
 
 template <int M, int SPL>
