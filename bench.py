@@ -1235,9 +1235,11 @@ def run_gemm(args):
     """The learned initializer's largest layer product: 4,096 windows' features
     (K = 8,256 for M = 16) times the 256 x 8,256 first-layer weights, BF16 with
     FP32 accumulation, bias and ReLU, FP32 and BF16 outputs (mdhp_gemm_bf16),
-    on the tensor-core engine (tcgen05) and on the warp-level MMA engine.  Each
-    launch is timed alone with CUDA events after a 256 MB write that flushes
-    L2; value = TFLOP/s of the tensor-core engine (2 M N K per launch)."""
+    on the tensor-core engine (tcgen05; operands by TMA), the same with
+    per-thread copies, and the warp-level MMA engine.  Each launch is timed
+    alone with CUDA events after a 256 MB write that flushes L2; value =
+    TFLOP/s of the tensor-core engine (2 M N K per launch, the K split's
+    clearing and finishing launches included in the time)."""
     import torch
 
     from paper_2411_10258_gb300.api import gemm_bf16, gemm_check
@@ -1257,7 +1259,7 @@ def run_gemm(args):
     sampler = ClockSampler(0, os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None,
                            name="gemm")
     with sampler:
-        for name, engine in (("tcgen05", 0), ("mma_sync", 1)):
+        for name, engine in (("tcgen05", 0), ("tcgen05_copies", 2), ("mma_sync", 1)):
             for _ in range(max(args.warmup, 3)):
                 gemm_bf16(A, W, M, N, K, bias=bias, relu=True, C=C, C_bf16=Cb, engine=engine)
             torch.cuda.synchronize()
@@ -1287,10 +1289,11 @@ def run_gemm(args):
                    "l2": "flushed (256 MB write) before every timed launch"},
         "roofline": {"bound": "tensor", "achieved": tc["tflops"], "peak": peak, "unit": "TFLOP/s",
                      "frac": tc["tflops"] / peak, "traffic": None,
-                     "kernel": "k_gemm_tc (tcgen05.mma, TMEM accumulators) + k_gemm_finish",
+                     "kernel": "k_gemm_tma (TMA + tcgen05.mma, TMEM accumulators) + k_gemm_finish",
                      "peak_source": f"{src}: MEASURED_PEAKS bf16 burst (cuBLAS)"},
         "engines": res, "max_abs_err_first_64_rows": err,
-        "gpu_launches": None, "clocks": sampler.summary()}), flush=True)
+        "gpu_launches": 2 * max(args.steps, 10),  # product kernel + split-K finishing kernel per step
+        "clocks": sampler.summary()}), flush=True)
 
 
 def main():

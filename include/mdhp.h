@@ -344,12 +344,16 @@ mdhp_status mdhp_init_model_set_gemm(mdhp_init_model *model, int32_t engine);
  * copy of the result, nullable; ignored when accumulate = 1).
  * engine 0: fifth-generation tensor cores (tcgen05.mma, accumulators in tensor
  * memory; 128 x up-to-256 tiles, K split over CTAs when the tiles alone do not
- * fill the GPU, in which case C is required and holds the partial sums).  It
- * needs 16-byte aligned A and B, lda and ldb multiples of 8, K a multiple of
- * 8 and, for an M/N-contiguous operand, M (resp. N) a multiple of 8; other
- * shapes return MDHP_E_UNSUPPORTED.  engine 1: warp-level MMA (mma.sync) on
- * 64 x 64 tiles, any layout.  Asynchronous on `stream`.  Errors: NULL
- * operands, sizes < 1, engine outside 0..1 (MDHP_E_ARG).
+ * fill the GPU, in which case C is required and holds the partial sums); with
+ * both operands K-contiguous the tiles are loaded by the tensor-memory
+ * accelerator (cp.async.bulk.tensor, 128-byte swizzle), otherwise by 16-byte
+ * copies from every thread.  It needs 16-byte aligned A and B, lda and ldb
+ * multiples of 8, K a multiple of 8 and, for an M/N-contiguous operand, M
+ * (resp. N) a multiple of 8; other shapes return MDHP_E_UNSUPPORTED.
+ * engine 1: warp-level MMA (mma.sync) on 64 x 64 tiles, any layout.  engine
+ * 2: as 0 with the 16-byte copies for every layout (for comparison).
+ * Asynchronous on `stream`.  Errors: NULL operands, sizes < 1, engine
+ * outside 0..2 (MDHP_E_ARG).
  */
 mdhp_status mdhp_gemm_bf16(const void *A, int64_t lda, int32_t a_mn, const void *B, int64_t ldb,
                            int32_t b_mn, int32_t M, int32_t N, int32_t K, const float *bias,

@@ -74,7 +74,7 @@ __device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, in
   __syncthreads();
   // walk the chunk in time order from its entering state; x_n = state at t_n
   Walker<M, BM, false> wk;
-  wk.load_beta(sm.bl2, 0);
+  wk.template load_beta<1>(sm.bl2, 0);  // one thread holds every source: slot j = source j
 #pragma unroll
   for (int j = 0; j < M; ++j) wk.R[j] = sm.encR[c * M + j];
   float tprev = sm.anc[c];

@@ -35,10 +35,12 @@ constexpr int kBins = 32;
 // tensor-core GEMM (mdhp_gemm_tc.cu)
 bool gemm_tc_supported(const void *A, int64_t lda, int a_mn, const void *B, int64_t ldb, int b_mn, int Mm,
                        int Nn, int Kk);
+// staging 0: TMA boxes for K-major operands (else per-thread 16-byte copies); 1: always the copies
 mdhp_status gemm_tc(const __nv_bfloat16 *A, int64_t lda, int a_mn, const __nv_bfloat16 *B, int64_t ldb,
                     int b_mn, int Mm, int Nn, int Kk, const float *bias, int relu, float *Cf,
-                    __nv_bfloat16 *Cb, int64_t ldc, int accumulate, int split, cudaStream_t st);
-int gemm_tc_launches(int Mm, int Nn, int Kk, int accumulate, int split);
+                    __nv_bfloat16 *Cb, int64_t ldc, int accumulate, int split, cudaStream_t st,
+                    int staging);
+int gemm_tc_launches(int Mm, int Nn, int Kk, int accumulate, int split, int a_mn, int b_mn, int staging);
 
 __host__ __device__ inline int init_k0(int M) {
   const int K = M + kBins * M * M + 3;
@@ -503,7 +505,7 @@ struct mdhp_init_model {
   float *h[4] = {}, *dh[4] = {}, *aux = nullptr, *loss = nullptr;
   __nv_bfloat16 *dhb[4] = {};
   int64_t step = 0;
-  int gemm_engine = 1;  // 0: tensor cores (tcgen05) where the layouts allow; 1: mma.sync
+  int gemm_engine = 0;  // 0: tensor cores (tcgen05) where the layouts allow; 1: mma.sync
 };
 
 static mdhp_status init_fail(mdhp_status s, const char *msg) {
@@ -552,7 +554,7 @@ static TcRoute tc_route(int engine, const __nv_bfloat16 *A, int64_t sam, int64_t
   r.b_mn = sbk == 1 ? 0 : 1;
   r.lda = r.a_mn ? sak : sam;
   r.ldb = r.b_mn ? sbk : sbn;
-  const bool out_ok = Cf != nullptr || gemm_tc_launches(Mm, Nn, Kk, accumulate, 0) == 1;
+  const bool out_ok = Cf != nullptr || gemm_tc_launches(Mm, Nn, Kk, accumulate, 0, r.a_mn, r.b_mn, 0) == 1;
   r.use = out_ok && gemm_tc_supported(A, r.lda, r.a_mn, B, r.ldb, r.b_mn, Mm, Nn, Kk);
   return r;
 }
@@ -562,7 +564,7 @@ static int gemm_launches(int engine, const __nv_bfloat16 *A, int64_t sam, int64_
                          const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, int Mm, int Nn, int Kk,
                          const float *Cf, int accumulate) {
   const TcRoute r = tc_route(engine, A, sam, sak, B, sbk, sbn, Mm, Nn, Kk, Cf, accumulate);
-  return r.use ? gemm_tc_launches(Mm, Nn, Kk, accumulate, 0) : 1;
+  return r.use ? gemm_tc_launches(Mm, Nn, Kk, accumulate, 0, r.a_mn, r.b_mn, 0) : 1;
 }
 
 // A product on the tensor cores (tcgen05) when tc_route allows it, else on
@@ -574,7 +576,7 @@ static mdhp_status launch_gemm(int engine, const __nv_bfloat16 *A, int64_t sam, 
   const TcRoute r = tc_route(engine, A, sam, sak, B, sbk, sbn, Mm, Nn, Kk, Cf, accumulate);
   if (r.use)
     return gemm_tc(A, r.lda, r.a_mn, B, r.ldb, r.b_mn, Mm, Nn, Kk, bias, relu, Cf, Cb, ldc, accumulate,
-                   0, st);
+                   0, st, 0);
   launch_gemm_mma(A, sam, sak, B, sbk, sbn, Mm, Nn, Kk, bias, relu, Cf, Cb, ldc, accumulate, st);
   return MDHP_OK;
 }
@@ -886,17 +888,18 @@ mdhp_status mdhp_gemm_bf16(const void *A, int64_t lda, int32_t a_mn, const void 
                            int32_t b_mn, int32_t M, int32_t N, int32_t K, const float *bias,
                            int32_t relu, float *C, void *C_bf16, int64_t ldc, int32_t accumulate,
                            int32_t engine, void *stream) {
-  if (!A || !B || M < 1 || N < 1 || K < 1 || engine < 0 || engine > 1 || (!C && (accumulate || !C_bf16)))
+  if (!A || !B || M < 1 || N < 1 || K < 1 || engine < 0 || engine > 2 || (!C && (accumulate || !C_bf16)))
     return init_fail(MDHP_E_ARG, "mdhp_gemm_bf16: bad argument");
   const __nv_bfloat16 *a = (const __nv_bfloat16 *)A, *b = (const __nv_bfloat16 *)B;
   __nv_bfloat16 *cb = accumulate ? nullptr : (__nv_bfloat16 *)C_bf16;
   cudaStream_t st = (cudaStream_t)stream;
-  if (engine == 0) {
+  if (engine == 0 || engine == 2) {
     if (!gemm_tc_supported(A, lda, a_mn, B, ldb, b_mn, M, N, K))
       return init_fail(MDHP_E_UNSUPPORTED, "mdhp_gemm_bf16: layout not supported by the tensor-core GEMM");
-    if (!C && gemm_tc_launches(M, N, K, accumulate, 0) > 1)
+    if (!C && gemm_tc_launches(M, N, K, accumulate, 0, a_mn, b_mn, engine == 2 ? 1 : 0) > 1)
       return init_fail(MDHP_E_ARG, "mdhp_gemm_bf16: this shape splits K and needs the FP32 output");
-    return gemm_tc(a, lda, a_mn, b, ldb, b_mn, M, N, K, bias, relu, C, cb, ldc, accumulate, 0, st);
+    return gemm_tc(a, lda, a_mn, b, ldb, b_mn, M, N, K, bias, relu, C, cb, ldc, accumulate, 0, st,
+                   engine == 2 ? 1 : 0);
   }
   const int64_t sam = a_mn ? 1 : lda, sak = a_mn ? lda : 1;
   const int64_t sbk = b_mn ? ldb : 1, sbn = b_mn ? 1 : ldb;

@@ -501,7 +501,29 @@ __device__ __forceinline__ double block_sum_double(double v, double *red) {
 }
 
 // ---------------------------------------------------------------------------
-// Per-thread recursion over MS sources starting at `base` (MS % 4 == 0).
+// Which sources a thread of a chunk holds.  The M sources form M/4 groups of
+// 4; thread s of the chunk's SPL threads holds groups s, s + SPL, s + 2 SPL,
+// ... (MS/4 of them), its state slot jj being source src_of(s, jj).  With
+// this interleaving the SPL threads that read an alpha row together read
+// SPL consecutive 16-byte groups at every step (no bank conflict), where
+// contiguous slices of MS sources would put threads s and s + 4 on the same
+// banks once MS >= 8.  (For MS = 4 both are the same mapping.)
+// ---------------------------------------------------------------------------
+template <int SPL>
+__device__ __forceinline__ int src_of(int s, int jj) {
+  static_assert((SPL & (SPL - 1)) == 0, "threads per chunk: a power of two");
+  return 4 * (s + SPL * (jj >> 2)) + (jj & 3);
+}
+// the slot of source u in thread s, or -1 when another thread of the chunk holds it
+template <int SPL>
+__device__ __forceinline__ int slot_of(int s, int u) {
+  const int g = u >> 2;
+  return (g & (SPL - 1)) == s ? 4 * (g / SPL) + (u & 3) : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Per-thread recursion over MS sources (MS % 4 == 0), slot jj = source
+// src_of(s, jj).
 // ---------------------------------------------------------------------------
 template <int MS, int BM, bool LEARN>
 struct Walker {
@@ -511,11 +533,12 @@ struct Walker {
   float b2[BM == 0 ? 1 : MS];  // beta * log2(e)
   float bmax;                   // the largest of b2
 
-  __device__ __forceinline__ void load_beta(const float *bl2, int base) {
+  template <int SPL>
+  __device__ __forceinline__ void load_beta(const float *bl2, int s) {
     bmax = 0.f;
 #pragma unroll
     for (int jj = 0; jj < (BM == 0 ? 1 : MS); ++jj) {
-      b2[jj] = bl2[BM == 0 ? 0 : base + jj];
+      b2[jj] = bl2[BM == 0 ? 0 : src_of<SPL>(s, jj)];
       bmax = fmaxf(bmax, b2[jj]);
     }
   }
@@ -552,8 +575,8 @@ struct Walker {
       }
     }
   }
-  // R += w * e_u restricted to my sources; u_rel = u - (first source of this
-  // thread), outside [0, MS) for another thread's source
+  // R += w * e_u restricted to my sources; u_rel = slot_of(s, u), outside
+  // [0, MS) for another thread's source
   __device__ __forceinline__ void add(int u_rel, float w) {
 #pragma unroll
     for (int jj = 0; jj < MS; ++jj) R[jj] += (jj == u_rel) ? w : 0.f;
@@ -575,30 +598,29 @@ __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float 
                                             const EV &ev, const Sm<M> &sm) {
   constexpr int MS = M / SPL;
   constexpr int AP = M + 4;
-  const int base = s * MS;
   if constexpr (BM == 0) {
     // one decay factor serves every source: walk the chunk from a0 (one
     // exponential per distinct timestamp)
     Walker<MS, BM, LEARN> wk;
-    wk.load_beta(sm.bl2, base);
+    wk.template load_beta<SPL>(sm.bl2, s);
     wk.zero();
     float tprev = a0;
     int gs = b0;
     for (int n = b0; n < b1; ++n) {
       const float tn = ev.time(n);
       if (tn > tprev) {
-        for (int k = gs; k < n; ++k) wk.add(ev.id(k) - base, ev.wt(k));
+        for (int k = gs; k < n; ++k) wk.add(slot_of<SPL>(s, ev.id(k)), ev.wt(k));
         wk.decay(tn - tprev);
         tprev = tn;
         gs = n;
       }
     }
-    for (int k = gs; k < b1; ++k) wk.add(ev.id(k) - base, ev.wt(k));
+    for (int k = gs; k < b1; ++k) wk.add(slot_of<SPL>(s, ev.id(k)), ev.wt(k));
     if (a1 > tprev) wk.decay(a1 - tprev);
 #pragma unroll
     for (int jj = 0; jj < MS; ++jj) {
-      sm.encR[c * M + base + jj] = wk.R[jj];
-      if (LEARN) sm.encS[c * M + base + jj] = wk.S[jj];
+      sm.encR[c * M + src_of<SPL>(s, jj)] = wk.R[jj];
+      if (LEARN) sm.encS[c * M + src_of<SPL>(s, jj)] = wk.S[jj];
     }
     return;
   }
@@ -612,8 +634,8 @@ __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float 
         (SPL >= 32) ? 0xffffffffu : (((1u << SPL) - 1u) << ((threadIdx.x & 31) & ~(SPL - 1)));
 #pragma unroll
     for (int jj = 0; jj < MS; ++jj) {
-      sm.encR[c * M + base + jj] = 0.f;
-      if (LEARN) sm.encS[c * M + base + jj] = 0.f;
+      sm.encR[c * M + src_of<SPL>(s, jj)] = 0.f;
+      if (LEARN) sm.encS[c * M + src_of<SPL>(s, jj)] = 0.f;
     }
     __syncwarp(gmask);
     for (int n = b0 + s; n < b1; n += SPL) {
@@ -633,10 +655,11 @@ __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float 
     if (LEARN) S[jj] = 0.f;
   }
   for (int n = b0; n < b1; ++n) {
-    const int u = ev.id(n) - base;
+    const int uid = ev.id(n);
+    const int u = slot_of<SPL>(s, uid);
     if ((unsigned)u < (unsigned)MS) {
       const float d = a1 - ev.time(n);
-      const float we = ev.wt(n) * exp2_acc(-sm.bl2[BM == 0 ? 0 : base + u] * d);
+      const float we = ev.wt(n) * exp2_acc(-sm.bl2[BM == 0 ? 0 : uid] * d);
 #pragma unroll
       for (int jj = 0; jj < MS; ++jj) {
         if (u == jj) {
@@ -648,8 +671,8 @@ __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float 
   }
 #pragma unroll
   for (int jj = 0; jj < MS; ++jj) {
-    sm.encR[c * M + base + jj] = R[jj];
-    if (LEARN) sm.encS[c * M + base + jj] = S[jj];
+    sm.encR[c * M + src_of<SPL>(s, jj)] = R[jj];
+    if (LEARN) sm.encS[c * M + src_of<SPL>(s, jj)] = S[jj];
   }
 }
 
@@ -727,17 +750,16 @@ __device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float 
   constexpr int NQ = MS / 4;
   constexpr int AP = M + 4;
   constexpr bool PRIV = UsePriv<M>::value;
-  const int base = s * MS;
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
   const int lane = tid & 31;
   const unsigned gmask = (SPL >= 32) ? 0xffffffffu : (((1u << SPL) - 1u) << (lane & ~(SPL - 1)));
   Walker<MS, BM, LEARN> wk;
-  wk.load_beta(sm.bl2, base);
+  wk.template load_beta<SPL>(sm.bl2, s);
 #pragma unroll
   for (int jj = 0; jj < MS; ++jj) {
-    wk.R[jj] = sm.encR[c * M + base + jj];
-    if (LEARN) wk.S[jj] = sm.encS[c * M + base + jj];
+    wk.R[jj] = sm.encR[c * M + src_of<SPL>(s, jj)];
+    if (LEARN) wk.S[jj] = sm.encS[c * M + src_of<SPL>(s, jj)];
   }
   float4 *gp = reinterpret_cast<float4 *>(sm.gpriv);
   ev.chunk_begin(c, s, b0, b1, gmask);  // streamed events: start this chunk's copies
@@ -751,22 +773,22 @@ __device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float 
     ev.next(n, tn, un);
     if (tn > tprev) {
       if (n - gs == 1) {
-        wk.add(pu - base, pw);
+        wk.add(pu, pw);
       } else {
-        for (int k = gs; k < n; ++k) wk.add(ev.id(k) - base, ev.wt(k));
+        for (int k = gs; k < n; ++k) wk.add(slot_of<SPL>(s, ev.id(k)), ev.wt(k));
       }
       wk.decay(tn - tprev);
       tprev = tn;
       gs = n;
     }
-    pu = un;
+    pu = slot_of<SPL>(s, un);
     pw = ev.wt(n);
-    const float4 *arow = reinterpret_cast<const float4 *>(sm.alpha + un * AP + base);
+    const float *arow = sm.alpha + un * AP + 4 * s;  // group s + SPL q of the row at step q
     float4 av[NQ];
     float d0 = 0.f, d1 = 0.f;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      av[q] = arow[q];
+      av[q] = *reinterpret_cast<const float4 *>(arow + 4 * SPL * q);
       d0 = fmaf(av[q].x, wk.R[4 * q + 0], d0);
       d1 = fmaf(av[q].y, wk.R[4 * q + 1], d1);
       d0 = fmaf(av[q].z, wk.R[4 * q + 2], d0);
@@ -797,7 +819,7 @@ __device__ __forceinline__ void pass2_chunk(int c, int s, int b0, int b1, float 
     } else {
       float *grow = sm.ga + un * ga_pitch(M);
 #pragma unroll
-      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[ga_col(base + jj)], r * wk.R[jj]);
+      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[ga_col(src_of<SPL>(s, jj))], r * wk.R[jj]);
     }
     if (LEARN) {
 #pragma unroll
@@ -958,7 +980,6 @@ __device__ __forceinline__ void pass2_fixed(int c, int s, int b0, int b1, const 
   constexpr int NQ = MS / 4;
   constexpr int AP = M + 4;
   constexpr bool PRIV = UsePriv<M>::value;
-  const int base = s * MS;
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
   const int lane = tid & 31;
@@ -967,7 +988,7 @@ __device__ __forceinline__ void pass2_fixed(int c, int s, int b0, int b1, const 
   const uint16_t *U = sm.ev_u;
   Walker<MS, 0, false> wk;
 #pragma unroll
-  for (int jj = 0; jj < MS; ++jj) wk.R[jj] = sm.encR[c * M + base + jj];
+  for (int jj = 0; jj < MS; ++jj) wk.R[jj] = sm.encR[c * M + src_of<SPL>(s, jj)];
   float4 *gp = reinterpret_cast<float4 *>(sm.gpriv);
   int gs = b0;
   int pu = 0;
@@ -978,21 +999,21 @@ __device__ __forceinline__ void pass2_fixed(int c, int s, int b0, int b1, const 
     const int un = cd & 0x7fff;
     if (cd & 0x8000) {
       if (n - gs == 1) {
-        wk.add(pu - base, pw);
+        wk.add(pu, pw);
       } else {
-        for (int k = gs; k < n; ++k) wk.add(((int)U[k] & 0x7fff) - base, w ? w[k] : 1.f);
+        for (int k = gs; k < n; ++k) wk.add(slot_of<SPL>(s, (int)U[k] & 0x7fff), w ? w[k] : 1.f);
       }
 #pragma unroll
       for (int jj = 0; jj < MS; ++jj) wk.R[jj] *= an;
       gs = n;
     }
-    pu = un;
+    pu = slot_of<SPL>(s, un);
     pw = w ? w[n] : 1.f;
-    const float4 *arow = reinterpret_cast<const float4 *>(sm.alpha + un * AP + base);
+    const float *arow = sm.alpha + un * AP + 4 * s;  // group s + SPL q of the row at step q
     float d0 = 0.f, d1 = 0.f;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      const float4 av = arow[q];
+      const float4 av = *reinterpret_cast<const float4 *>(arow + 4 * SPL * q);
       d0 = fmaf(av.x, wk.R[4 * q + 0], d0);
       d1 = fmaf(av.y, wk.R[4 * q + 1], d1);
       d0 = fmaf(av.z, wk.R[4 * q + 2], d0);
@@ -1023,7 +1044,7 @@ __device__ __forceinline__ void pass2_fixed(int c, int s, int b0, int b1, const 
     } else {
       float *grow = sm.ga + un * ga_pitch(M);
 #pragma unroll
-      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[ga_col(base + jj)], r * wk.R[jj]);
+      for (int jj = 0; jj < MS; ++jj) atomicAdd(&grow[ga_col(src_of<SPL>(s, jj))], r * wk.R[jj]);
     }
   }
 }
@@ -1066,7 +1087,7 @@ __device__ void evaluate(int NC, const EV &ev, float T, int Mrt, Sm<M> &sm, floa
         atomicAdd(&sm.gb[0], acc);
       } else {
 #pragma unroll
-        for (int jj = 0; jj < MS; ++jj) atomicAdd(&sm.gb[s * MS + jj], gbl[jj]);
+        for (int jj = 0; jj < MS; ++jj) atomicAdd(&sm.gb[src_of<SPL>(s, jj)], gbl[jj]);
       }
     }
   }
@@ -1135,7 +1156,7 @@ __device__ __forceinline__ float alpha_event_sum(int i, int j, const Sm<M> &sm) 
     constexpr int MS = M / SPL;
     constexpr int NQ = MS / 4;
     const int NT = blockDim.x, NC = NT / SPL;
-    const int s = j / MS, jj = j % MS, q = jj / 4, e = jj % 4;
+    const int g = j >> 2, s = g % SPL, q = g / SPL, e = j & 3;  // j = src_of(s, 4 q + e)
     const float *base = sm.gpriv + ((i * NQ + q) * NT) * 4 + e;
     float acc = 0.f;
     for (int c = 0; c < NC; ++c) acc += base[(c * SPL + s) * 4];
