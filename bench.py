@@ -76,8 +76,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--path", default="auto", choices=["auto", "recursion"],
                     help="--workload 5fixed: kernel family of the fixed-beta fit")
-    ap.add_argument("--threads", type=int, default=0, help="--workload 5fixed: threads per window")
-    ap.add_argument("--chunk-threads", type=int, default=0, help="--workload 5fixed: threads per chunk")
+    ap.add_argument("--threads", type=int, default=0, help="--workload 5fixed or 3: threads per window")
+    ap.add_argument("--chunk-threads", type=int, default=0, help="--workload 5fixed or 3: threads per chunk")
     ap.add_argument("--cutoff", type=int, default=-1, help="--workload 5fixed: shared-memory cutoff (events)")
     ap.add_argument("--no-split", action="store_true", help="--workload 5fixed: one launch, no split")
     ap.add_argument("--event-ring", action="store_true",
@@ -538,6 +538,8 @@ def run_long_learned(args):
     beta0 = torch.from_numpy(p["beta"]).float().to(dev)
     plan = Plan(M, 1, B, 0)
     plan.set_event_ring(args.event_ring)
+    if args.threads > 0 and args.chunk_threads > 0:  # a stated launch shape (default: the plan's)
+        plan.set_shape(args.threads, args.chunk_threads, args.cutoff if args.cutoff >= 0 else 8192)
     opts = FitOptions(optimizer=1, max_iters=args.iters, lr=1e-2, init=1, fit_beta=1)
     mu = torch.zeros(B, M, device=dev)
     al = torch.zeros(B, M, M, device=dev)

@@ -120,6 +120,22 @@ static int num_sms() {
   return v;
 }
 
+// the most threads per block a kernel was compiled for (its launch bound)
+static int kernel_max_threads(const void *fn) {
+  cudaFuncAttributes fa{};
+  if (!fn || cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return fa.maxThreadsPerBlock;
+}
+
+// both recursion fit kernels (staged and streamed events) of this split take nt threads
+static bool fit_takes(int Mt, int spl, int BM, bool learn, int nt) {
+  const FitFn a = get_fit(Mt, spl, BM, learn, true), b = get_fit(Mt, spl, BM, learn, false);
+  return a && b && kernel_max_threads((const void *)a) >= nt && kernel_max_threads((const void *)b) >= nt;
+}
+
 static mdhp_status prepare_kernel(const void *fn, int smem) {
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
@@ -760,6 +776,10 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *p, int32_t nt, int32_t spl, int32_t c
   // (matrix beta runs only the decoupled kernels, which have no chunk split)
   if (p->beta_mode != MDHP_BETA_MATRIX && !get_fit(p->Mt, spl, p->beta_mode, false, true))
     return fail(MDHP_E_UNSUPPORTED, "threads per chunk %d not built for M<=%d", spl, p->Mt);
+  if (p->beta_mode != MDHP_BETA_MATRIX &&
+      !(fit_takes(p->Mt, spl, p->beta_mode, false, nt) && fit_takes(p->Mt, spl, p->beta_mode, true, nt)))
+    return fail(MDHP_E_UNSUPPORTED, "%d threads per window exceed the kernel for %d threads per chunk", nt,
+                spl);
   if (cutoff < 0) return fail(MDHP_E_ARG, "cutoff < 0");
   p->shape = Shape{nt, spl, cutoff};
   if (nt >= 64 && nt <= 256 && (nt & (nt - 1)) == 0 && nt >= p->Mt) p->xnt = nt;
@@ -924,7 +944,8 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   if (p->timing) cudaEventRecord(p->ev_t0, st);
   if (need_long) {
     FitFn fl = get_fit(p->Mt, sh.spl, p->beta_mode, learn, false);
-    if (!fl) return fail(MDHP_E_UNSUPPORTED, "no streamed fit kernel for this shape");
+    if (!fl || kernel_max_threads((const void *)fl) < sh.nt)
+      return fail(MDHP_E_UNSUPPORTED, "no streamed fit kernel for this shape");
     FitArgs al = a;
     al.queue = p->ctl + 0;
     al.range = p->ctl + 2;
@@ -954,7 +975,8 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
   }
   {
     FitFn fs = get_fit(p->Mt, sh.spl, p->beta_mode, learn, true);
-    if (!fs) return fail(MDHP_E_UNSUPPORTED, "no staged fit kernel for this shape");
+    if (!fs || kernel_max_threads((const void *)fs) < sh.nt)
+      return fail(MDHP_E_UNSUPPORTED, "no staged fit kernel for this shape");
     FitArgs as = a;
     as.queue = p->ctl + 1;
     as.range = p->ctl + 4;
@@ -1053,9 +1075,7 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
         if (p->xdual && sp[0] != nt && nt < 256) cands.push_back({nt, 0, 0, 0, 0, 1, sp[0], sp[1]});
     } else {
       for (int spl = 1; spl <= 32; spl *= 2) {
-        if (nt % spl || !get_fit(p->Mt, spl, p->beta_mode, learn, true) ||
-            !get_fit(p->Mt, spl, p->beta_mode, learn, false))
-          continue;
+        if (nt % spl || !fit_takes(p->Mt, spl, p->beta_mode, learn, nt)) continue;
         const int fit = stage_fit(p, nt, spl, batch->weights != nullptr, learn, adam);
         const int dflt = default_shape(p->Mt).cutoff;
         cands.push_back({nt, spl, 0, 0, 0, 0, 256, 1});

@@ -49,24 +49,39 @@ __host__ __device__ inline int init_k0(int M) {
 
 // ---------------------------------------------------------------------------
 // Features.  One CTA per window, NT threads = NT chunks of the window.
+// PACK: two 16-bit bin counters per 32-bit word (half the shared memory, so
+// two CTAs of 256 threads fit an SM at M = 32); taken when the batch states
+// max_events < 65,536, since no bin then exceeds 65,535 counts.  A window
+// longer than that bound gets an all-zero histogram block (its shares, log N,
+// log T and beta are still set).
 // ---------------------------------------------------------------------------
-template <int M>
-__global__ void __launch_bounds__(128) k_features(const int64_t *offsets, const float *t,
-                                                  const int16_t *id, const float *Tspan,
-                                                  const float *beta, int beta_stride, int Mrt,
-                                                  int K0, __nv_bfloat16 *X, float *aux) {
+constexpr int kFeatThreads = 256;
+
+template <int M, bool PACK>
+__device__ __forceinline__ int hist_count(const uint32_t *hist, int q) {
+  return PACK ? (int)((hist[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu) : (int)hist[q];
+}
+
+template <int M, bool PACK>
+__global__ void __launch_bounds__(kFeatThreads) k_features(const int64_t *offsets, const float *t,
+                                                           const int16_t *id, const float *Tspan,
+                                                           const float *beta, int beta_stride, int Mrt,
+                                                           int K0, __nv_bfloat16 *X, float *aux) {
+  static_assert((M & (M - 1)) == 0 && kBins == 32, "power-of-two M, 32 bins");
+  constexpr int kWords = PACK ? M * M * kBins / 2 : M * M * kBins;
   extern __shared__ __align__(16) unsigned char smem[];
-  int *hist = reinterpret_cast<int *>(smem);            // [M][M][kBins]
-  float *lastc = reinterpret_cast<float *>(hist + M * M * kBins);  // [NT][M]
-  int *cnt = reinterpret_cast<int *>(lastc + blockDim.x * M);      // [M]
-  float *invtot = reinterpret_cast<float *>(cnt + M);              // [M][M]
+  uint32_t *hist = reinterpret_cast<uint32_t *>(smem);                 // [M][M][kBins] counts
+  float *lastc = reinterpret_cast<float *>(hist + kWords);             // [NT][M]
+  int *cnt = reinterpret_cast<int *>(lastc + blockDim.x * M);          // [M]
+  float *invtot = reinterpret_cast<float *>(cnt + M);                  // [M][M]
   const int b = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
   const int64_t o0 = offsets[b];
   const int N = (int)(offsets[b + 1] - o0);
   const float T = Tspan[b];
   const float *tt = t + o0;
   const int16_t *uu = id + o0;
-  for (int p = tid; p < M * M * kBins; p += NT) hist[p] = 0;
+  const bool hist_on = !PACK || N < 65536;
+  for (int p = tid; p < kWords / 4; p += NT) reinterpret_cast<uint4 *>(hist)[p] = make_uint4(0, 0, 0, 0);
   for (int j = tid; j < M; j += NT) cnt[j] = 0;
   __syncthreads();
   // chunk c = [b0, b1), boundaries moved past tie groups
@@ -105,7 +120,7 @@ __global__ void __launch_bounds__(128) k_features(const int64_t *offsets, const 
   const float scale = (T > 0.f && N > 0) ? (float)N / T : 1.f;
   int gs = b0;
   float tcur = (b0 < b1) ? tt[b0] : 0.f;
-  for (int n = b0; n < b1; ++n) {
+  for (int n = hist_on ? b0 : b1; n < b1; ++n) {
     const float tn = tt[n];
     if (tn > tcur) {  // the previous tie group becomes history
       for (int k = gs; k < n; ++k) {
@@ -126,35 +141,51 @@ __global__ void __launch_bounds__(128) k_features(const int64_t *offsets, const 
         // and the clamp below both land in bin 0)
         int bin = gap > 0.f ? ((__float_as_int(gap) >> 23) & 0xff) - 127 + kBins / 2 : 0;
         bin = bin < 0 ? 0 : (bin >= kBins ? kBins - 1 : bin);
-        atomicAdd(&hist[(i * M + j) * kBins + bin], 1);
+        const int q = (i * M + j) * kBins + bin;
+        if (PACK) atomicAdd(&hist[q >> 1], 1u << ((q & 1) * 16));
+        else atomicAdd(&hist[q], 1u);
       }
     }
   }
   __syncthreads();
   for (int pair = tid; pair < M * M; pair += NT) {  // row totals of each histogram, once
     int tot = 0;
-    for (int k = 0; k < kBins; ++k) tot += hist[pair * kBins + k];
+    for (int k = 0; k < kBins; ++k) tot += hist_count<M, PACK>(hist, pair * kBins + k);
     invtot[pair] = tot > 0 ? 1.f / (float)tot : 0.f;
   }
   __syncthreads();
-  __nv_bfloat16 *row = X + (size_t)b * K0;
+  // the row, eight BF16 values (one 16-byte store) per step; K0 % 64 == 0
+  uint4 *row = reinterpret_cast<uint4 *>(X + (size_t)b * K0);
   const float invN = N > 0 ? 1.f / (float)N : 0.f;
-  for (int p = tid; p < K0; p += NT) {
-    float v = 0.f;
-    if (p < Mrt) {
-      v = (float)cnt[p] * invN;
-    } else if (p >= M && p < M + M * M * kBins) {
-      const int q = p - M, pair = q / kBins;
-      const int i = pair / M, j = pair % M;
-      if (i < Mrt && j < Mrt) v = (float)hist[q] * invtot[pair];
-    } else if (p == M + M * M * kBins) {
-      v = logf((float)(N > 0 ? N : 1));
-    } else if (p == M + M * M * kBins + 1) {
-      v = logf(T > 0.f ? T : 1.f);
-    } else if (p == M + M * M * kBins + 2) {
-      v = beta[(int64_t)b * beta_stride];
+  constexpr int kHist0 = M, kHist1 = M + M * M * kBins;
+  for (int v8 = tid; v8 < K0 / 8; v8 += NT) {
+    uint32_t packed[4];
+#pragma unroll
+    for (int e2 = 0; e2 < 4; ++e2) {
+      float two[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = v8 * 8 + e2 * 2 + h;
+        float v = 0.f;
+        if (p < Mrt) {
+          v = (float)cnt[p] * invN;
+        } else if (p >= kHist0 && p < kHist1) {
+          const int q = p - kHist0, pair = q / kBins;
+          const int i = pair / M, j = pair % M;
+          if (i < Mrt && j < Mrt) v = (float)hist_count<M, PACK>(hist, q) * invtot[pair];
+        } else if (p == kHist1) {
+          v = logf((float)(N > 0 ? N : 1));
+        } else if (p == kHist1 + 1) {
+          v = logf(T > 0.f ? T : 1.f);
+        } else if (p == kHist1 + 2) {
+          v = beta[(int64_t)b * beta_stride];
+        }
+        two[h] = v;
+      }
+      const __nv_bfloat162 bb = __floats2bfloat162_rn(two[0], two[1]);
+      packed[e2] = *reinterpret_cast<const uint32_t *>(&bb);
     }
-    row[p] = __float2bfloat16(v);
+    row[v8] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
   }
   for (int i = tid; i < Mrt; i += NT) aux[(int64_t)b * Mrt + i] = 0.5f * (float)max(cnt[i], 1) / T;
 }
@@ -701,17 +732,24 @@ mdhp_status mdhp_init_features(const mdhp_batch *batch, const float *beta, void 
   if (batch->B <= 0) return MDHP_OK;
   const int M = batch->M, Mt = M <= 4 ? 4 : M <= 8 ? 8 : M <= 16 ? 16 : 32;
   const int K0 = init_k0(M);
-  const int nt = 128;
-  const int smem = (Mt * Mt * kBins + nt * Mt + Mt + Mt * Mt) * 4;
+  const int nt = kFeatThreads;
+  const bool pack = batch->max_events > 0 && batch->max_events < 65536;
+  const int words = pack ? Mt * Mt * kBins / 2 : Mt * Mt * kBins;
+  const int smem = (words + nt * Mt + Mt + Mt * Mt) * 4;
   const int bstride = batch->beta_mode == MDHP_BETA_SCALAR ? 1 : M;
   cudaStream_t st = (cudaStream_t)stream;
-#define MDHP_FEAT(MV)                                                                             \
-  case MV:                                                                                        \
+#define MDHP_FEAT_P(MV, PK)                                                                       \
+  {                                                                                               \
     if (smem > 48 * 1024)                                                                         \
-      cudaFuncSetAttribute(k_features<MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);    \
-    k_features<MV><<<batch->B, nt, smem, st>>>(batch->offsets, batch->t, batch->id,               \
-                                               batch->T_span, beta, bstride, M, K0,               \
-                                               (__nv_bfloat16 *)features_bf16, mu_cold);          \
+      cudaFuncSetAttribute(k_features<MV, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    k_features<MV, PK><<<batch->B, nt, smem, st>>>(batch->offsets, batch->t, batch->id,           \
+                                                   batch->T_span, beta, bstride, M, K0,           \
+                                                   (__nv_bfloat16 *)features_bf16, mu_cold);      \
+  }
+#define MDHP_FEAT(MV)                  \
+  case MV:                             \
+    if (pack) MDHP_FEAT_P(MV, true)    \
+    else MDHP_FEAT_P(MV, false)        \
     break;
   switch (Mt) {
     MDHP_FEAT(4)
@@ -719,6 +757,7 @@ mdhp_status mdhp_init_features(const mdhp_batch *batch, const float *beta, void 
     MDHP_FEAT(16)
     MDHP_FEAT(32)
   }
+#undef MDHP_FEAT_P
 #undef MDHP_FEAT
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return init_fail(MDHP_E_CUDA, cudaGetErrorString(e));
