@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--workload", default="5", choices=["2", "3", "4", "5", "5fixed", "6", "attack", "lstm", "gemm"],
                     help="5 (default): warm vs cold fits to tolerance; 2: fixed-iteration fits")
     ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--warm-lr", type=float, default=None,
+                    help="headline: the warm arm's Adam step (default: --lr, the same as the cold arm)")
     ap.add_argument("--lr", type=float, default=HEADLINE_LR,
                     help="Adam step of the headline fits (the paper leaves the optimiser open; "
                          "8e-2 measured fastest to the tolerance for the cold arm)")
@@ -872,7 +874,8 @@ def run_headline(args):
         # arm's graph (sibling nodes) does not keep, and the cold arm keeps
         # the same kernel family so the two arms differ only in their start
         plans[name].set_split(False)
-        opts[name] = FitOptions(tol=args.tol, optimizer=HEADLINE_OPTS["optimizer"], lr=args.lr,
+        lr = args.warm_lr if (name == "warm" and args.warm_lr) else args.lr
+        opts[name] = FitOptions(tol=args.tol, optimizer=HEADLINE_OPTS["optimizer"], lr=lr,
                                 max_iters=HEADLINE_OPTS["max_iters"], **kw)
         tuned[name] = None if args.no_autotune else plans[name].autotune(
             db, opts[name], torch.zeros(B, M, device=dev), torch.zeros(B, M, M, device=dev),
