@@ -630,6 +630,11 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
       // evaluation returns the last finite point theta_{k-1}
       b1t *= a.b1;
       b2t *= a.b2;
+      // Adam's bias corrections as two reciprocals per iteration; per
+      // parameter the step takes the approximate square root and reciprocal
+      // (relative error near 2^-22 in the step, which only sets where the next
+      // point lies; the likelihood and its gradient are exact as before)
+      const float c1 = 1.f / (1.f - b1t), c2 = 1.f / (1.f - b2t);
       Ps = 0.f;
       Pc = 0.f;
       for (int p = tid; p < M + M * M; p += NT) {
@@ -651,8 +656,7 @@ __global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
           const float m2 = a.b2 * sm.av[pc] + (1.f - a.b2) * gs * gs;
           sm.am[pc] = m1;
           sm.av[pc] = m2;
-          const float mh = m1 / (1.f - b1t), vh = m2 / (1.f - b2t);
-          step = a.lr * mh / (sqrtf(vh) + a.eps);
+          step = a.lr * (m1 * c1) * rcp_ftz(sqrt_ftz(m2 * c2) + a.eps);
         } else {
           step = a.lr * gs;
         }

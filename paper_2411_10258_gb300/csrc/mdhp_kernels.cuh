@@ -247,6 +247,7 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
     if (sm.ctl[2]) { ++k; break; }
     b1t *= a.b1;
     b2t *= a.b2;
+    const float c1 = 1.f / (1.f - b1t), c2 = 1.f / (1.f - b2t);  // Adam bias corrections
     for (int p = tid; p < nupd; p += blockDim.x) {
       const float g = gbp[p] * invN;
       float &th = param_ref<M>(p, Mrt, sm);
@@ -256,8 +257,7 @@ __device__ void fit_window(const FitArgs &a, int b, int N, float T, const EV &ev
         const float m2 = a.b2 * avp[p] + (1.f - a.b2) * g * g;
         amp[p] = m1;
         avp[p] = m2;
-        const float mh = m1 / (1.f - b1t), vh = m2 / (1.f - b2t);
-        step = a.lr * mh / (sqrtf(vh) + a.eps);
+        step = a.lr * (m1 * c1) * rcp_ftz(sqrt_ftz(m2 * c2) + a.eps);  // as in the decoupled fit
       } else {
         step = a.lr * g;
       }

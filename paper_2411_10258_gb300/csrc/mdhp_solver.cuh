@@ -108,6 +108,13 @@ __device__ __forceinline__ float rcp_ftz(float x) {
   return y;
 }
 
+// approximate square root (PTX sqrt.approx, flush-to-zero) of a second moment >= 0
+__device__ __forceinline__ float sqrt_ftz(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   const float y = x - c;
   const float t = s + y;
