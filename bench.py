@@ -179,7 +179,7 @@ class ClockSampler:
 # which fits the headline's own windows (seed 2024, rank 0) cold, to the same
 # tolerance, in launch shape T threads per window, one launch; keyed by T.
 # Summary: profiles/k_fit_x_M32_dram_headline_fit.md.
-HEADLINE_FIT_DRAM = {128: 1.61e12 + 20.25e9, 256: 927.84e9 + 12.67e9}
+HEADLINE_FIT_DRAM = {128: 1.81e12 + 24.81e9, 256: 926.65e9 + 12.74e9}
 
 
 def measured_peaks():
@@ -1029,11 +1029,11 @@ def run_headline(args):
                 "feature_read_gbs": feat_gbs,
                 "feature_read_frac_of_hbm": feat_gbs / float(hbm_peak.get("hbm_gbs", 6800.0)),
                 "hbm_peak_source": f"{hbm_src}: MEASURED_PEAKS copy bandwidth",
-                "measured_limiter": "the feature stream (128 B per event-iteration, from L2 and "
-                                    "DRAM) at 8-16 warps per SM: neither DRAM bandwidth (a "
-                                    "128-thread fit reads 1.6 TB from DRAM, 0.57 of the copy "
-                                    "bandwidth; a 256-thread fit 0.94 TB in the same time) nor "
-                                    "the FMA pipe binds; latency does (profiles/)"}
+                "measured_limiter": "latency of the feature loads and the per-event FMA chains "
+                                    "at 12 warps per SM (128 threads, three CTAs): neither DRAM "
+                                    "bandwidth (1.8 TB per fit, 0.75 of the copy bandwidth; a "
+                                    "256-thread fit reads 0.94 TB in about the same time) nor the "
+                                    "FMA pipe binds (profiles/)"}
     line = {"metric": METRIC, "value": res["warm"]["fits_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["warm"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -441,8 +441,21 @@ __device__ __forceinline__ float xseg_sum(int i, int j, const Sm<M> &sm) {
 
 enum : int { XM_GLOBAL = 0, XM_SHARED = 1, XM_RING = 2 };
 
+// Residency: the streamed M = 32 fit is bound by how many warps per SM keep
+// feature loads and their dependent FMA chains in flight, so the 128-thread
+// build is held to 168 registers for three CTAs per SM (12 warps; shared
+// memory allows three): 355 ms against 373 ms at two CTAs for the 65,536-
+// window fit to 1e-5.  The 256-thread build keeps its registers (two CTAs
+// would leave 128 and spill 428 bytes).
+template <int M, int NTC>
+struct XBounds {
+  static constexpr bool three = NTC == 128 && M >= 32;
+  static constexpr int threads = three ? 128 : 256;
+  static constexpr int ctas = three ? 3 : (M >= 32 ? 1 : 2);
+};
+
 template <int M, int BM, int XM, int NTC>
-__global__ void __launch_bounds__(256, (M >= 32 ? 1 : 2)) k_fit_x(FitArgs a) {
+__global__ void __launch_bounds__(XBounds<M, NTC>::threads, XBounds<M, NTC>::ctas) k_fit_x(FitArgs a) {
   constexpr bool XS = XM == XM_SHARED;
   extern __shared__ __align__(16) unsigned char smem[];
   Sm<M> sm;
