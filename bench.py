@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--chunk-threads", type=int, default=0, help="--workload 5fixed or 3: threads per chunk")
     ap.add_argument("--cutoff", type=int, default=-1, help="--workload 5fixed: shared-memory cutoff (events)")
     ap.add_argument("--no-split", action="store_true", help="--workload 5fixed: one launch, no split")
+    ap.add_argument("--feature-store", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="--workload 5fixed: first feature steps in tensor memory (1), then also in "
+                         "shared memory (2), or neither (0)")
     ap.add_argument("--to-tol", action="store_true",
                     help="--workload 5fixed: fit to --tol (at most 3,000 evaluations) instead of --iters")
     ap.add_argument("--event-ring", action="store_true",
@@ -177,9 +180,10 @@ class ClockSampler:
 # from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of
 #   python bench.py --workload 5fixed --windows 65536 --to-tol --steps 1 --threads T --no-split
 # which fits the headline's own windows (seed 2024, rank 0) cold, to the same
-# tolerance, in launch shape T threads per window, one launch; keyed by T.
+# tolerance, in launch shape T threads per window, one launch, feature store S
+# (--feature-store S); keyed by (T, S).
 # Summary: profiles/k_fit_x_M32_dram_headline_fit.md.
-HEADLINE_FIT_DRAM = {128: 1.81e12 + 24.81e9, 256: 926.65e9 + 12.74e9}
+HEADLINE_FIT_DRAM = {(128, 0): 1.81e12 + 24.81e9, (256, 0): 926.65e9 + 12.74e9}
 
 
 def measured_peaks():
@@ -1001,14 +1005,15 @@ def run_headline(args):
     traffic, traffic_note = args.traffic, "DRAM read + write of one fit given with --traffic"
     cold_shape = tuned.get("cold") or {}
     if traffic is None:
-        key = cold_shape.get("threads_per_window")
+        key = (cold_shape.get("threads_per_window"), cold_shape.get("feature_store", 0))
         if (world == 1 and B == 65536 and M == 32 and args.lr == HEADLINE_LR and args.tol == 1e-5
                 and cold_shape.get("path") == "decoupled" and not cold_shape.get("split")
+                and cold_shape.get("pipe_stages", 0) == 0 and cold_shape.get("cutoff", 0) == 0
                 and key in HEADLINE_FIT_DRAM):
             traffic = HEADLINE_FIT_DRAM[key]
             traffic_note = (f"DRAM read + write of this fit (same windows, options and launch shape: "
-                            f"{key} threads per window, one launch) from an ncu capture "
-                            "(profiles/k_fit_x_M32_dram_headline_fit.md)")
+                            f"{key[0]} threads per window, one launch, feature store {key[1]}) from an "
+                            "ncu capture (profiles/k_fit_x_M32_dram_headline_fit.md)")
         else:
             traffic_note = "no DRAM capture of this launch shape"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -1245,6 +1250,8 @@ def run_fixed_headline(args):
         plan.set_split(False)
     elif args.split_threads:
         plan.set_split(True, args.split_threads, 1)
+    if args.feature_store >= 0:
+        plan.set_feature_store(args.feature_store)
     beta = torch.from_numpy(p["beta"].astype(np.float32)).to(dev)
     if args.to_tol:  # the headline's cold fit: to the tolerance, at most 3,000 evaluations
         opts = FitOptions(optimizer=HEADLINE_OPTS["optimizer"], lr=args.lr, max_iters=3000, tol=args.tol, init=1)
@@ -1263,6 +1270,7 @@ def run_fixed_headline(args):
         print(json.dumps({"fit": r, "fit_kernel_ms": ms, "event_iterations_per_s": ev / (ms / 1e3),
                           "event_iterations": ev,
                           "shape": plan.shape(), "split": plan.split(), "path": args.path,
+                          "feature_store": plan.get_feature_store(),
                           "invalid_windows": int((out["status"] != 0).sum().item())}), flush=True)
 
 

@@ -219,7 +219,10 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
  * fits), the feature ring (none; 1x4, 2x3, 2x4, 4x3 steps x stages) and the
  * two-launch split (off; 256 x 1, 256 x 2, 128 x 1, 128 x 2 long threads x CTAs per
  * SM; not tried when the plan's split was disabled with mdhp_plan_set_split before the
- * call); for the event recursion every built threads-per-chunk split and the
+ * call), and at template width 32 the tensor-memory feature store
+ * (mdhp_plan_set_feature_store 1 and 2; 256 threads, no ring, no split; the
+ * choice is read back with mdhp_plan_get_feature_store); for the event
+ * recursion every built threads-per-chunk split and the
  * staging cutoff (none, the default, the largest that fits).  One warm-up
  * run comes first.  With opts->tol == 0 each candidate runs tune_iters
  * iterations (<= 0: 20) on every window.  With opts->tol > 0 each candidate
@@ -393,6 +396,29 @@ mdhp_status mdhp_plan_set_path(mdhp_plan *plan, int32_t path);
 mdhp_status mdhp_plan_set_pipeline(mdhp_plan *plan, int32_t steps_per_stage, int32_t stages);
 mdhp_status mdhp_plan_get_pipeline(const mdhp_plan *plan, int32_t *steps_per_stage,
                                    int32_t *stages);
+
+/* Feature store of the decoupled kernels' streamed windows (Sec. IV-B.3
+ * Stage 1, "Decoupling": the beta-only features are computed once per fit
+ * and read at every iteration).  Applies to the single-launch shapes without
+ * a feature ring (mdhp_plan_set_pipeline stages = 0) at template width 32
+ * (M 17..32) with 256 threads per window; other shapes ignore it.
+ *   store = 0 (default): every feature step is re-read from the plan's
+ *             scratch at every iteration.
+ *   store = 1: the first steps of every thread (one 32-float row per step)
+ *             stay in the SM's tensor memory, 512 columns per SM shared
+ *             evenly by the CTAs resident on it (8 steps per thread for the
+ *             one 256-thread CTA per SM); the kernel
+ *             allocates the columns when its CTA starts and frees them before
+ *             it exits (a CTA waits for its columns while another kernel on
+ *             the same SM holds them).
+ *   store = 2: as 1, and the next steps stay in the shared memory the
+ *             kernel's other data leave at its occupancy.
+ * Only the remaining steps are re-read from the scratch.  Results do not
+ * depend on the choice beyond the order of the per-thread log-intensity sums
+ * (rounding only).  MDHP_E_ARG for store outside {0, 1, 2}. */
+mdhp_status mdhp_plan_set_feature_store(mdhp_plan *plan, int32_t store);
+/* The setting above, or -1 for a NULL plan. */
+int32_t mdhp_plan_get_feature_store(const mdhp_plan *plan);
 
 /* Streamed events of the event recursion (windows without a stated bound, or
  * longer than the staging cutoff; beta learned, or MDHP_PATH_RECURSION):

@@ -61,6 +61,8 @@ SIGNATURES = [
     ("mdhp_plan_autotune", ctypes.c_int, [P, ctypes.POINTER(MdhpBatch), ctypes.POINTER(MdhpFitOpts),
                                           P, P, P, P, P, P, ctypes.c_int32, P, P, P]),
     ("mdhp_plan_set_pipeline", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32]),
+    ("mdhp_plan_set_feature_store", ctypes.c_int, [P, ctypes.c_int32]),
+    ("mdhp_plan_get_feature_store", ctypes.c_int32, [P]),
     ("mdhp_plan_get_pipeline", ctypes.c_int, [P, P, P]),
     ("mdhp_plan_set_split", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     ("mdhp_plan_get_split", ctypes.c_int, [P, P, P, P]),

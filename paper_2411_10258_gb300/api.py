@@ -266,7 +266,7 @@ class Plan:
         return dict(path=("decoupled", "recursion")[chosen[0]], threads_per_window=chosen[1],
                     threads_per_chunk=chosen[2], cutoff=chosen[3], pipe_steps=chosen[4],
                     pipe_stages=chosen[5], split=bool(chosen[6]), split_threads=chosen[7],
-                    split_ctas=chosen[8], ms=best.value)
+                    split_ctas=chosen[8], feature_store=self.get_feature_store(), ms=best.value)
 
     def set_event_ring(self, enable: bool):
         """Streamed events through the bulk-copy ring (mdhp_plan_set_event_ring)."""
@@ -276,6 +276,16 @@ class Plan:
     def set_wait_limit(self, polls: int):
         """Bound of the bulk-copy rings' consumer waits (mdhp_plan_set_wait_limit); 0 = default."""
         _lib.check(self.lib.mdhp_plan_set_wait_limit(self.h, polls), "mdhp_plan_set_wait_limit")
+
+    def set_feature_store(self, store: int):
+        """Where the decoupled kernels keep each thread's first feature steps
+        (mdhp_plan_set_feature_store): 0 the scratch only, 1 tensor memory,
+        2 tensor memory and then shared memory."""
+        _lib.check(self.lib.mdhp_plan_set_feature_store(self.h, int(store)),
+                   "mdhp_plan_set_feature_store")
+
+    def get_feature_store(self) -> int:
+        return int(self.lib.mdhp_plan_get_feature_store(self.h))
 
     def set_pipeline(self, steps_per_stage: int, stages: int):
         """Feature ring of the decoupled kernels (mdhp_plan_set_pipeline); stages=0: none."""

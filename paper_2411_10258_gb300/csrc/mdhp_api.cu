@@ -202,6 +202,11 @@ struct mdhp_plan {
   // 6 bytes of event data, and the ring's shared-memory reads measured slower
   // than cached global loads)
   int ev_ring = 0;
+  // decoupled fit, single launch of streamed features: the first feature
+  // steps of every thread live in tensor memory (512 columns per SM shared
+  // by the resident CTAs) instead of being re-read from the scratch at
+  // every iteration
+  int xtmem = 0;
   uint32_t wait_polls = 0;           // consumer waits on the bulk-copy rings (0: default bound)
   mdhp_init_model *model = nullptr;  // learned initializer (not owned)
   std::string cache;                 // autotune cache file ("" = none)
@@ -341,6 +346,8 @@ void tune_load(mdhp_plan *p) {
           p->xnt_long = ntl;
           p->xcta_long = cl;
         }
+        const int fs = field_int(e.second, "feature_store", p->xtmem);
+        if (fs >= 0 && fs <= 2) p->xtmem = fs;
       }
       if (path == 1) apply_recursion(p, nt, spl, cut);
     }
@@ -350,6 +357,7 @@ void tune_load(mdhp_plan *p) {
 
 struct TuneChoice {
   int nt, spl, cut, ps, pd, dual, ntl, cl;
+  int tm = 0;  // decoupled: feature steps in tensor memory (mdhp_plan_set_feature_store)
 };
 
 bool tune_store(const mdhp_plan *p, int path, const TuneChoice &c, float ms) {
@@ -362,8 +370,9 @@ bool tune_store(const mdhp_plan *p, int path, const TuneChoice &c, float ms) {
   snprintf(line, sizeof(line),
            "{\"key\": \"%s\", \"threads_per_window\": %d, \"threads_per_chunk\": %d, "
            "\"smem_cutoff_events\": %d, \"pipe_steps\": %d, \"pipe_stages\": %d, "
-           "\"split\": %d, \"split_threads\": %d, \"split_ctas\": %d, \"ms\": %.4f}",
-           key.c_str(), c.nt, c.spl, c.cut, c.ps, c.pd, c.dual, c.ntl, c.cl, ms);
+           "\"split\": %d, \"split_threads\": %d, \"split_ctas\": %d, \"feature_store\": %d, "
+           "\"ms\": %.4f}",
+           key.c_str(), c.nt, c.spl, c.cut, c.ps, c.pd, c.dual, c.ntl, c.cl, c.tm, ms);
   bool found = false;
   for (auto &e : v)
     if (e.first == key) {
@@ -727,6 +736,15 @@ mdhp_status mdhp_plan_set_pipeline(mdhp_plan *p, int32_t steps_per_stage, int32_
   return MDHP_OK;
 }
 
+mdhp_status mdhp_plan_set_feature_store(mdhp_plan *p, int32_t tmem) {
+  if (!p) return fail(MDHP_E_ARG, "plan NULL");
+  if (tmem < 0 || tmem > 2) return fail(MDHP_E_ARG, "feature store %d (0, 1 or 2)", tmem);
+  p->xtmem = tmem;
+  return MDHP_OK;
+}
+
+int32_t mdhp_plan_get_feature_store(const mdhp_plan *p) { return p ? p->xtmem : -1; }
+
 int32_t mdhp_plan_last_launches(const mdhp_plan *p) { return p ? p->launches : -1; }
 
 mdhp_status mdhp_plan_set_split(mdhp_plan *p, int32_t enable, int32_t long_threads,
@@ -902,18 +920,42 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
         al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1, 0, 0, p->beta_mode == 2);
       }
       FitFn fx = get_fitx(p->Mt, p->beta_mode, al.pipe_stages > 0 ? XM_RING : XM_GLOBAL, p->xnt);
-      if ((s = prepare_kernel((const void *)fx, al.carve.total)) != MDHP_OK) return s;
+      FitFn ft = (p->xtmem && al.pipe_stages == 0) ? get_fitx(p->Mt, p->beta_mode, XM_TMEM, p->xnt)
+                                                   : nullptr;
+      if (ft) fx = ft;
+      int dyn = al.carve.total;
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fx, p->xnt, dyn);
+      if (ft) {
+        // each resident CTA's share of the 512 tensor-memory columns (a
+        // power of two) and, with feature store 2, of the shared memory the
+        // carve leaves at this occupancy: steps of NT float4 slices
+        int cols = 512;
+        while (cols > 32 && cols * std::max(occ, 1) > 512) cols >>= 1;
+        al.tmem_cols = cols;
+        if (cols * std::max(occ, 1) > 512 || cols / std::max(p->xnt / 128, 1) < p->Mt)
+          return fail(MDHP_E_UNSUPPORTED, "tensor-memory features: %d CTAs per SM leave no row", occ);
+        al.smem_steps = 0;
+        if (p->xtmem == 2) {
+          int dev = 0, smem_sm = 0;
+          cudaGetDevice(&dev);
+          cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+          const int step_bytes = p->Mt * 4 * p->xnt;
+          const int room = std::min(smem_sm / std::max(occ, 1) - 1024, max_dyn_smem()) - dyn;
+          al.smem_steps = std::max(0, std::min(room / step_bytes, 64));
+          dyn += al.smem_steps * step_bytes;
+        }
+      }
+      if ((s = prepare_kernel((const void *)fx, dyn)) != MDHP_OK) return s;
       cudaStream_t ls = st;
       if (xres > 0) {
         cudaEventRecord(p->ev_fork, st);
         cudaStreamWaitEvent(p->side, p->ev_fork, 0);
         ls = p->side;
       }
-      int occ = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fx, p->xnt, al.carve.total);
       int gl = num_sms() * (occ > 0 ? occ : 1);
       if (gl > p->xgrid) gl = p->xgrid;
-      fx<<<gl, p->xnt, al.carve.total, ls>>>(al);
+      fx<<<gl, p->xnt, dyn, ls>>>(al);
       ++p->launches;
       if ((s = cuda_check("k_fit_x (global features)")) != MDHP_OK) return s;
       if (xres > 0) cudaEventRecord(p->ev_join, p->side);
@@ -1070,6 +1112,12 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
         if (fit >= 64) cands.push_back({nt, 0, fit, pd[0], pd[1], 0, 256, 1});
       }
       if (fit >= 128) cands.push_back({nt, 0, fit / 2 / 32 * 32, 0, 0, 0, 256, 1});
+      if (p->beta_mode != 2 && get_fitx(p->Mt, p->beta_mode, XM_TMEM, nt)) {
+        for (int tm = 1; tm <= 2; ++tm) {
+          cands.push_back({nt, 0, 0, 0, 0, 0, 256, 1, tm});
+          if (fit >= 64) cands.push_back({nt, 0, fit, 0, 0, 0, 256, 1, tm});
+        }
+      }
       static const int kSplits[][2] = {{256, 1}, {256, 2}, {128, 1}, {128, 2}};
       for (const auto &sp : kSplits)  // a split the caller disabled is not a candidate
         if (p->xdual && sp[0] != nt && nt < 256) cands.push_back({nt, 0, 0, 0, 0, 1, sp[0], sp[1]});
@@ -1093,7 +1141,7 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
   const Shape shape0 = p->shape;
   const int xnt0 = p->xnt, xres0 = p->xres, timing0 = p->timing;
   const int ps0 = p->pipe_steps, pd0 = p->pipe_stages;
-  const int du0 = p->xdual, ntl0 = p->xnt_long, cl0 = p->xcta_long;
+  const int du0 = p->xdual, ntl0 = p->xnt_long, cl0 = p->xcta_long, tm0 = p->xtmem;
   p->timing = 0;
   float best = -1.f;
   Cand win{0, 0, 0, 0, 0, 0, 256, 1};
@@ -1109,6 +1157,7 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
       p->xdual = cd.dual;
       p->xnt_long = cd.ntl;
       p->xcta_long = cd.cl;
+      p->xtmem = cd.tm;
     }
     copy_params(false);
     cudaEventRecord(e0, st);
@@ -1139,6 +1188,7 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
   p->xdual = du0;
   p->xnt_long = ntl0;
   p->xcta_long = cl0;
+  p->xtmem = tm0;
   copy_params(false);
   cudaStreamSynchronize(st);
   cudaFree(snap);
@@ -1153,6 +1203,7 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
     p->xdual = win.dual;
     p->xnt_long = win.ntl;
     p->xcta_long = win.cl;
+    p->xtmem = win.tm;
   } else {
     apply_recursion(p, win.nt, win.spl, win.cut);
   }

@@ -21,6 +21,7 @@
 
 #include "mdhp_async.cuh"
 #include "mdhp_solver.cuh"
+#include "mdhp_tmem.cuh"
 
 namespace mdhp {
 
@@ -439,7 +440,81 @@ __device__ __forceinline__ float xseg_sum(int i, int j, const Sm<M> &sm) {
   return acc;
 }
 
-enum : int { XM_GLOBAL = 0, XM_SHARED = 1, XM_RING = 2 };
+enum : int { XM_GLOBAL = 0, XM_SHARED = 1, XM_RING = 2, XM_TMEM = 3 };
+
+// One evaluation with the features of every thread in three tiers: steps
+// [0, Kt) in tensor memory (row tb of this thread's lane, M columns per
+// step), steps [Kt, Kt + Ks) in shared memory (XSt, step-major like the
+// global scratch), the rest read from the global scratch as in xpass.  The
+// tensor-memory loads are warp-collective, so every thread walks all Kt
+// steps (Kt is the same for the whole CTA) and only the threads whose range
+// covers a step use it.  The log-intensities are added to the compensated
+// sum in pairs, as in xpass.
+template <int M, int NTC>
+__device__ __forceinline__ void xpass_t(int p0, int p1, int i0, const float4 *X, const float4 *XSt,
+                                        XMap m, uint32_t tb, int Kt, int Ks, const Sm<M> &sm,
+                                        float &Ls, float &Lc) {
+  constexpr int NQ = M / 4;
+  const bool active = p0 < p1;
+  const int NT = NTC > 0 ? NTC : m.NT;
+  XAcc<M> acc;
+  if (active) acc.begin(i0, sm);
+  float pend = 0.f;
+  // tensor memory: one load and its wait per step (measured faster than
+  // keeping the next step's load in flight, which needs 32 more registers)
+  for (int k = 0; k < Kt; ++k) {
+    float4 x[NQ];
+    __syncwarp();
+    tm_ld<NQ>(tb + (uint32_t)(k * M), x);
+    if (p0 + k < p1) {
+      const float lg = acc.event(p0 + k, x, sm);
+      if (k & 1) kahan_add(Ls, Lc, pend + lg);
+      else pend = lg;
+    }
+  }
+  int cnt = active ? min(Kt, p1 - p0) : 0;  // events added so far (odd: pend is pending)
+  const int ps = NQ * NT;
+  for (int k = Kt; k < Kt + Ks && p0 + k < p1; ++k) {  // shared-memory tier
+    float4 x[NQ];
+    const float4 *px = XSt + (size_t)(k - Kt) * ps + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) x[q] = px[q * NT];
+    const float lg = acc.event(p0 + k, x, sm);
+    if (cnt & 1) kahan_add(Ls, Lc, pend + lg);
+    else pend = lg;
+    ++cnt;
+  }
+  if (cnt & 1) kahan_add(Ls, Lc, pend);
+  int p = p0 + Kt + Ks;
+  if (p < p1) {  // the steps past both tiers: global, one step ahead
+    const float4 *px = X + threadIdx.x + (size_t)(Kt + Ks) * ps;
+    float4 xa[NQ], xb[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) xa[q] = px[q * NT];
+    for (;;) {
+      const bool hb = p + 1 < p1;
+      if (hb) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) xb[q] = px[ps + q * NT];
+      }
+      const float la = acc.event(p, xa, sm);
+      if (!hb) {
+        kahan_add(Ls, Lc, la);
+        break;
+      }
+      const bool ha = p + 2 < p1;
+      if (ha) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) xa[q] = px[2 * ps + q * NT];
+      }
+      kahan_add(Ls, Lc, la + acc.event(p + 1, xb, sm));
+      if (!ha) break;
+      p += 2;
+      px += 2 * ps;
+    }
+  }
+  if (active) acc.flush(sm);
+}
 
 // Residency: the streamed M = 32 fit is bound by how many warps per SM keep
 // feature loads and their dependent FMA chains in flight, so the 128-thread
@@ -447,16 +522,17 @@ enum : int { XM_GLOBAL = 0, XM_SHARED = 1, XM_RING = 2 };
 // memory allows three): 355 ms against 373 ms at two CTAs for the 65,536-
 // window fit to 1e-5.  The 256-thread build keeps its registers (two CTAs
 // would leave 128 and spill 428 bytes).
-template <int M, int NTC>
+template <int M, int NTC, int XM>
 struct XBounds {
-  static constexpr bool three = NTC == 128 && M >= 32;
+  static constexpr bool three = NTC == 128 && M >= 32 && XM != XM_TMEM;
   static constexpr int threads = three ? 128 : 256;
   static constexpr int ctas = three ? 3 : (M >= 32 ? 1 : 2);
 };
 
 template <int M, int BM, int XM, int NTC>
-__global__ void __launch_bounds__(XBounds<M, NTC>::threads, XBounds<M, NTC>::ctas) k_fit_x(FitArgs a) {
+__global__ void __launch_bounds__(XBounds<M, NTC, XM>::threads, XBounds<M, NTC, XM>::ctas) k_fit_x(FitArgs a) {
   constexpr bool XS = XM == XM_SHARED;
+  constexpr bool XT = XM == XM_TMEM;
   extern __shared__ __align__(16) unsigned char smem[];
   Sm<M> sm;
   sm.bind(smem, a.carve);
@@ -480,6 +556,26 @@ __global__ void __launch_bounds__(XBounds<M, NTC>::threads, XBounds<M, NTC>::cta
       mbar_init_fence();
     }
     __syncthreads();
+  }
+  // tensor-memory feature rows: a.tmem_cols columns for this CTA (the host
+  // sizes them so that every CTA resident on an SM gets its share of 512);
+  // lane = tid mod 128, and threads sharing a lane split its columns
+  uint32_t tb = 0;
+  int tsteps = 0;
+  // shared-memory tier of the same mode: a.smem_steps steps per thread after
+  // the carve, [step][slice][thread]
+  float4 *xst = XT ? reinterpret_cast<float4 *>(smem + a.carve.total) : nullptr;
+  if constexpr (XT) {
+    if (tid < 32) {
+      tm_alloc((uint32_t)__cvta_generic_to_shared(sm.ctl + 8), (uint32_t)a.tmem_cols);
+      tm_relinquish();
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const int share = NT > 128 ? a.tmem_cols / (NT / 128) : a.tmem_cols;
+    tb = (uint32_t)sm.ctl[8] + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * share);
+    tsteps = share / M;
   }
   for (;;) {
     if (tid == 0) {
@@ -548,6 +644,22 @@ __global__ void __launch_bounds__(XBounds<M, NTC>::threads, XBounds<M, NTC>::cta
       else build_features<M, BM, false>(N, ev, Mrt, sm, Xg, xcap, xm);
     }
     if (pipe) fence_proxy_async_global();  // this thread's feature stores -> the copy engine
+    const int Kt = XT ? min(L, tsteps) : 0;
+    const int Ks = XT ? min(L - Kt, a.smem_steps) : 0;
+    if constexpr (XT) {  // this thread's first Kt + Ks steps: global scratch -> its rows
+      __syncwarp();
+      for (int k = 0; k < Kt; ++k) {
+        float4 x[M / 4];
+#pragma unroll
+        for (int q = 0; q < M / 4; ++q) x[q] = Xg[(size_t)(k * (M / 4) + q) * NT + tid];
+        tm_st<M / 4>(tb + (uint32_t)(k * M), x);
+      }
+      tm_wait_st();
+      for (int k = Kt; k < Kt + Ks; ++k)
+#pragma unroll
+        for (int q = 0; q < M / 4; ++q)
+          xst[(size_t)((k - Kt) * (M / 4) + q) * NT + tid] = Xg[(size_t)(k * (M / 4) + q) * NT + tid];
+    }
     const int p0 = min(tid * L, N), p1 = min(p0 + L, N);
     int i0 = 0;
     while (i0 < M - 1 && sm.tstart[i0 + 1] <= p0) ++i0;
@@ -604,6 +716,8 @@ __global__ void __launch_bounds__(XBounds<M, NTC>::threads, XBounds<M, NTC>::cta
           timed_out = true;
           break;
         }
+      } else if constexpr (XT) {
+        xpass_t<M, NTC>(p0, p1, i0, (const float4 *)Xg, xst, xm, tb, Kt, Ks, sm, Ls, Lc);
       } else {
         xpass<M, false, NTC>(p0, p1, i0, (const float4 *)Xg, xcap, xm, sm, Ls, Lc);
       }
@@ -704,6 +818,12 @@ __global__ void __launch_bounds__(XBounds<M, NTC>::threads, XBounds<M, NTC>::cta
       a.status[b] = wst;
     }
     __syncthreads();
+  }
+  if constexpr (XT) {  // every thread's tensor-memory accesses are complete
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (tid < 32) tm_dealloc((uint32_t)sm.ctl[8], (uint32_t)a.tmem_cols);
   }
 }
 

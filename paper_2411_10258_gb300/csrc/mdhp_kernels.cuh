@@ -57,6 +57,11 @@ struct FitArgs {
   // bulk-copy rings (features, events): polls of a consumer's wait, 0 = the
   // default bound (kWaitPolls suspending polls)
   uint32_t wait_polls;
+  // decoupled fit with tensor-memory feature rows (XM_TMEM): columns this CTA
+  // allocates (a power of two, 32..512; the CTAs resident on one SM together
+  // take at most 512)
+  int tmem_cols;
+  int smem_steps;  //   and steps per thread kept in shared memory after the carve
   Carve carve;
 };
 

@@ -1,0 +1,125 @@
+"""Decoupled fit with the first feature steps of every thread kept in tensor
+memory (mdhp_plan_set_feature_store).
+
+The features x_n = R(t_n) of a fixed-beta window (Sec. IV-B.3 Stage 1,
+"Decoupling") are computed once per fit; with the feature store on, the
+first steps of each thread's range live in the SM's tensor memory (and,
+with store 2, the next ones in shared memory) and only the rest is re-read
+from the plan's scratch at every iteration.  Windows
+shorter than the tensor-memory rows, windows that span both tiers, ragged
+tails, a width below the template's (M = 24 in the 32-wide kernel), scalar
+and per-source beta and both stores are fitted and compared
+
+* with the same plan with the feature store off (same statuses and
+  iteration counts; lnL within 1e-5 relative, parameters within 1e-4 of the
+  group's scale: only the order of the per-thread log sums differs), and
+* with the FP64 oracle re-fitting sampled windows from the same cold start
+  (lnL 1e-5 relative, parameters 1e-4 of the group's scale)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LL_RTOL = 1e-5
+P_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def mdhp():
+    import paper_2411_10258_gb300 as m
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return m
+
+
+def _batch(wl, M, mode, B, seed, lo, hi):
+    rng = np.random.default_rng(seed)
+    betas = np.full((B, 1), 1.0) if mode == 0 else rng.uniform(0.5, 2.0, (B, M))
+    mu, alpha = wl.sample_params(rng, B, M, mode, betas, rng.uniform(0.2, 0.8, B))
+    counts = wl.log_uniform_counts(rng, B, lo, hi)
+    return wl.simulate(M, mode, mu, alpha, betas, counts, seed=seed, stream=seed)
+
+
+def _fit(mdhp, bt, db, nt, store, iters):
+    M, B = bt.M, bt.B
+    plan = mdhp.Plan(M, bt.beta_mode, B, int(bt.counts.max()))
+    plan.set_split(False)
+    plan.set_shape(nt, 4, 0)  # every window streamed (no shared-memory class)
+    plan.set_feature_store(store)
+    assert plan.get_feature_store() == store
+    opts = mdhp.FitOptions(optimizer=1, max_iters=iters, lr=2e-2, init=1)
+    mu = torch.zeros(B, M, device="cuda")
+    al = torch.zeros(B, M, M, device="cuda")
+    be = torch.from_numpy(np.ascontiguousarray(bt.beta, dtype=np.float32)).cuda()
+    out = plan.fit(db, opts, mu, al, be)
+    torch.cuda.synchronize()
+    return (out["loglik"].cpu().numpy(), out["iters"].cpu().numpy(), out["status"].cpu().numpy(),
+            mu.cpu().numpy(), al.cpu().numpy())
+
+
+def _close_params(a, b, rtol):
+    scale = np.abs(b).max()
+    return np.all(np.abs(a - b) <= rtol * scale + 1e-30)
+
+
+@pytest.mark.parametrize("M,mode,nt,store", [(32, 0, 256, 1), (32, 0, 256, 2), (32, 1, 256, 2),
+                                              (24, 1, 256, 1)])
+def test_tmem_features_match_scratch_and_oracle(mdhp, wl, orc, M, mode, nt, store):
+    iters = 30
+    bt = _batch(wl, M, mode, 160, 4100 + M + 7 * mode + nt, 100, 6000)
+    db = mdhp.DeviceBatch.from_host(bt, "cuda")
+    ll_t, it_t, st_t, mu_t, al_t = _fit(mdhp, bt, db, nt, store, iters)
+    ll_g, it_g, st_g, mu_g, al_g = _fit(mdhp, bt, db, nt, 0, iters)
+    assert np.all(st_t == 0) and np.all(st_g == 0)
+    assert np.all(it_t == iters) and np.all(it_g == iters)
+    assert np.all(np.abs(ll_t - ll_g) <= LL_RTOL * np.abs(ll_g))
+    for b in range(bt.B):
+        assert _close_params(mu_t[b], mu_g[b], P_RTOL), b
+        assert _close_params(al_t[b], al_g[b], P_RTOL), b
+    # the FP64 oracle on the longest, the shortest and random windows
+    order = np.argsort(bt.counts, kind="stable")
+    rng = np.random.default_rng(M + nt)
+    sample = sorted(set(int(b) for b in list(order[-2:]) + list(order[:2]) + list(rng.choice(bt.B, 3, replace=False))))
+    o = orc.fit_opts(optimizer=1, max_iters=iters, lr=2e-2)
+    for b in sample:
+        t, ids, T, _ = bt.window(b)
+        beta_b = np.asarray(bt.beta[b], dtype=np.float64)
+        m0, a0 = orc.cold_init(ids, float(T), M, beta_b, mode=mode)
+        r = orc.fit(t, ids, float(T), m0, a0, beta_b, o, mode=mode)
+        assert r["iters"] == iters
+        assert abs(ll_t[b] - r["lnL"]) <= LL_RTOL * abs(r["lnL"]), (b, ll_t[b], r["lnL"])
+        rm = r["mu"]
+        assert np.all(np.abs(mu_t[b] - rm) <= P_RTOL * np.maximum(np.abs(rm), 1e-3 * np.abs(rm).max())), b
+        assert _close_params(al_t[b], r["alpha"], P_RTOL), b
+
+
+def test_tmem_features_fit_to_tolerance(mdhp, wl):
+    """A fit to tolerance (the benchmark's kind of fit) stops every window as
+    the scratch-only fit does, at nearly the same iteration."""
+    M, B = 32, 256
+    bt = _batch(wl, M, 0, B, 77, 100, 10000)
+    db = mdhp.DeviceBatch.from_host(bt, "cuda")
+    res = []
+    for store in (2, 0):
+        plan = mdhp.Plan(M, 0, B, int(bt.counts.max()))
+        plan.set_split(False)
+        plan.set_shape(256, 4, 0)
+        plan.set_feature_store(store)
+        opts = mdhp.FitOptions(optimizer=1, max_iters=3000, lr=8e-2, init=1, tol=1e-5)
+        mu = torch.zeros(B, M, device="cuda")
+        al = torch.zeros(B, M, M, device="cuda")
+        be = torch.from_numpy(np.ascontiguousarray(bt.beta, dtype=np.float32)).cuda()
+        out = plan.fit(db, opts, mu, al, be)
+        torch.cuda.synchronize()
+        res.append((out["loglik"].cpu().numpy(), out["iters"].cpu().numpy(), out["status"].cpu().numpy()))
+    (ll_t, it_t, st_t), (ll_g, it_g, st_g) = res
+    E_MAXITER = 6
+    assert np.all((st_t == 0) | (st_t == E_MAXITER)) and np.all((st_g == 0) | (st_g == E_MAXITER))
+    # the stopping rule compares successive lnL at 1e-5: rounding-order
+    # differences may move a window's stop by a few iterations
+    both = (st_t == 0) & (st_g == 0)
+    assert both.mean() >= 0.95
+    assert np.all(np.abs(it_t - it_g)[both] <= 0.1 * it_g[both] + 3)
+    assert np.all(np.abs(ll_t - ll_g) <= 1e-4 * np.abs(ll_g))
