@@ -183,7 +183,8 @@ class ClockSampler:
 # tolerance, in launch shape T threads per window, one launch, feature store S
 # (--feature-store S); keyed by (T, S).
 # Summary: profiles/k_fit_x_M32_dram_headline_fit.md.
-HEADLINE_FIT_DRAM = {(128, 0): 1.81e12 + 24.81e9, (256, 0): 926.65e9 + 12.74e9}
+HEADLINE_FIT_DRAM = {(128, 0): 1.81e12 + 24.81e9, (256, 0): 926.65e9 + 12.74e9,
+                     (256, 2): 189.462e9 + 11.065e9}
 
 
 def measured_peaks():
@@ -1034,11 +1035,16 @@ def run_headline(args):
                 "feature_read_gbs": feat_gbs,
                 "feature_read_frac_of_hbm": feat_gbs / float(hbm_peak.get("hbm_gbs", 6800.0)),
                 "hbm_peak_source": f"{hbm_src}: MEASURED_PEAKS copy bandwidth",
-                "measured_limiter": "latency of the feature loads and the per-event FMA chains "
-                                    "at 12 warps per SM (128 threads, three CTAs): neither DRAM "
-                                    "bandwidth (1.8 TB per fit, 0.75 of the copy bandwidth; a "
-                                    "256-thread fit reads 0.94 TB in about the same time) nor the "
-                                    "FMA pipe binds (profiles/)"}
+                "feature_store": cold_shape.get("feature_store", 0),
+                "measured_limiter": ("latency at one 256-thread CTA per SM (8 warps): the "
+                                     "per-iteration barriers and the loads of the feature steps "
+                                     "past the 2,816 events per window kept in tensor and shared "
+                                     "memory; DRAM (0.2 TB per fit) and the FMA pipe do not bind "
+                                     "(profiles/k_fit_x_M32_tmem_full_set_8192windows.md)")
+                                    if cold_shape.get("feature_store", 0) else
+                                    ("latency of the streamed feature loads and the per-event FMA "
+                                     "chains: neither DRAM bandwidth (0.9-1.8 TB per fit) nor the "
+                                     "FMA pipe binds (profiles/k_fit_x_M32_dram_headline_fit.md)")}
     line = {"metric": METRIC, "value": res["warm"]["fits_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["warm"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
