@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--chunk-threads", type=int, default=0, help="--workload 5fixed or 3: threads per chunk")
     ap.add_argument("--cutoff", type=int, default=-1, help="--workload 5fixed: shared-memory cutoff (events)")
     ap.add_argument("--no-split", action="store_true", help="--workload 5fixed: one launch, no split")
-    ap.add_argument("--feature-store", type=int, default=-1, choices=[-1, 0, 1, 2],
+    ap.add_argument("--feature-store", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="--workload 5fixed: first feature steps in tensor memory (1), then also in "
                          "shared memory (2), or neither (0)")
     ap.add_argument("--to-tol", action="store_true",
@@ -184,7 +184,7 @@ class ClockSampler:
 # (--feature-store S); keyed by (T, S).
 # Summary: profiles/k_fit_x_M32_dram_headline_fit.md.
 HEADLINE_FIT_DRAM = {(128, 0): 1.81e12 + 24.81e9, (256, 0): 926.65e9 + 12.74e9,
-                     (256, 2): 189.462e9 + 11.065e9}
+                     (256, 2): 189.462e9 + 11.065e9, (256, 3): 326.645e9 + 12.090e9}
 
 
 def measured_peaks():
@@ -1036,10 +1036,11 @@ def run_headline(args):
                 "feature_read_frac_of_hbm": feat_gbs / float(hbm_peak.get("hbm_gbs", 6800.0)),
                 "hbm_peak_source": f"{hbm_src}: MEASURED_PEAKS copy bandwidth",
                 "feature_store": cold_shape.get("feature_store", 0),
-                "measured_limiter": ("latency at one 256-thread CTA per SM (8 warps): the "
-                                     "per-iteration barriers and the loads of the feature steps "
-                                     "past the 2,816 events per window kept in tensor and shared "
-                                     "memory; DRAM (0.2 TB per fit) and the FMA pipe do not bind "
+                "measured_limiter": ("latency at one CTA per SM (8-12 warps): the per-iteration "
+                                     "update and its barriers (about 2 us per window-iteration) "
+                                     "and the loads of the feature steps past those kept in "
+                                     "tensor and shared memory; DRAM (0.2-0.34 TB per fit) and "
+                                     "the FMA pipe do not bind "
                                      "(profiles/k_fit_x_M32_tmem_full_set_8192windows.md)")
                                     if cold_shape.get("feature_store", 0) else
                                     ("latency of the streamed feature loads and the per-event FMA "

@@ -220,7 +220,7 @@ mdhp_status mdhp_plan_set_shape(mdhp_plan *plan, int32_t threads_per_window,
  * two-launch split (off; 256 x 1, 256 x 2, 128 x 1, 128 x 2 long threads x CTAs per
  * SM; not tried when the plan's split was disabled with mdhp_plan_set_split before the
  * call), and at template width 32 the tensor-memory feature store
- * (mdhp_plan_set_feature_store 1 and 2; 256 threads, no ring, no split; the
+ * (mdhp_plan_set_feature_store 1, 2 and 3; no ring, no split; the
  * choice is read back with mdhp_plan_get_feature_store); for the event
  * recursion every built threads-per-chunk split and the
  * staging cutoff (none, the default, the largest that fits).  One warm-up
@@ -401,7 +401,8 @@ mdhp_status mdhp_plan_get_pipeline(const mdhp_plan *plan, int32_t *steps_per_sta
  * Stage 1, "Decoupling": the beta-only features are computed once per fit
  * and read at every iteration).  Applies to the single-launch shapes without
  * a feature ring (mdhp_plan_set_pipeline stages = 0) at template width 32
- * (M 17..32) with 256 threads per window; other shapes ignore it.
+ * (M 17..32) with 256 threads per window (store 3: its own 384); other
+ * shapes ignore it.
  *   store = 0 (default): every feature step is re-read from the plan's
  *             scratch at every iteration.
  *   store = 1: the first steps of every thread (one 32-float row per step)
@@ -413,9 +414,13 @@ mdhp_status mdhp_plan_get_pipeline(const mdhp_plan *plan, int32_t *steps_per_sta
  *             the same SM holds them).
  *   store = 2: as 1, and the next steps stay in the shared memory the
  *             kernel's other data leave at its occupancy.
+ *   store = 3: as 2, with 384 threads per window (12 warps, 168 registers:
+ *             more loads in flight and fewer parameters per thread in the
+ *             update; 5 steps per thread in tensor memory).
  * Only the remaining steps are re-read from the scratch.  Results do not
- * depend on the choice beyond the order of the per-thread log-intensity sums
- * (rounding only).  MDHP_E_ARG for store outside {0, 1, 2}. */
+ * depend on the choice beyond rounding: stores 1 and 2 change only the order
+ * of the per-thread log-intensity sums; store 3 partitions the features over
+ * more threads.  MDHP_E_ARG for store outside {0, 1, 2, 3}. */
 mdhp_status mdhp_plan_set_feature_store(mdhp_plan *plan, int32_t store);
 /* The setting above, or -1 for a NULL plan. */
 int32_t mdhp_plan_get_feature_store(const mdhp_plan *plan);

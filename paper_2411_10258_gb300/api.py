@@ -280,7 +280,7 @@ class Plan:
     def set_feature_store(self, store: int):
         """Where the decoupled kernels keep each thread's first feature steps
         (mdhp_plan_set_feature_store): 0 the scratch only, 1 tensor memory,
-        2 tensor memory and then shared memory."""
+        2 tensor memory and then shared memory, 3 as 2 with 384 threads."""
         _lib.check(self.lib.mdhp_plan_set_feature_store(self.h, int(store)),
                    "mdhp_plan_set_feature_store")
 

@@ -33,6 +33,7 @@ FitFn get_fitx_m32(int BM, int xm, int nt) {
   if (xm == XM_RING) return BM == 0 ? k_fit_x<32, 0, XM_RING, 0> : k_fit_x<32, 1, XM_RING, 0>;
   if (xm == XM_TMEM) {  // tensor-memory feature rows: 256 threads, one CTA per SM
     if (nt == 256) return BM == 0 ? k_fit_x<32, 0, XM_TMEM, 256> : k_fit_x<32, 1, XM_TMEM, 256>;
+    if (nt == 384) return BM == 0 ? k_fit_x<32, 0, XM_TMEM, 384> : k_fit_x<32, 1, XM_TMEM, 384>;
     return nullptr;  // 128 threads at two CTAs per SM measured slower than the scratch alone
   }
   if (xm != XM_GLOBAL) return nullptr;

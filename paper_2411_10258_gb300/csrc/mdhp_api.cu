@@ -347,7 +347,7 @@ void tune_load(mdhp_plan *p) {
           p->xcta_long = cl;
         }
         const int fs = field_int(e.second, "feature_store", p->xtmem);
-        if (fs >= 0 && fs <= 2) p->xtmem = fs;
+        if (fs >= 0 && fs <= 3) p->xtmem = fs;
       }
       if (path == 1) apply_recursion(p, nt, spl, cut);
     }
@@ -616,9 +616,9 @@ mdhp_status mdhp_plan_create(mdhp_plan **out, int32_t M, int32_t beta_mode, int3
     if (slots > 0) {
       p->xgrid = slots;
       p->xcap = (int)max_events_per_window;
-      // per slot (xcap + 2 * 256) rows: the step-major layout pads each
+      // per slot (xcap + 2 * 384) rows: the step-major layout pads each
       // window to L * threads with L odd (see mdhp_fitx.cuh)
-      const size_t bytes = (size_t)p->xgrid * (size_t)(p->Mt / 4) * (size_t)(p->xcap + 512) *
+      const size_t bytes = (size_t)p->xgrid * (size_t)(p->Mt / 4) * (size_t)(p->xcap + 768) *
                            sizeof(float4);
       if (cudaMalloc(&p->xbuf, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -738,7 +738,7 @@ mdhp_status mdhp_plan_set_pipeline(mdhp_plan *p, int32_t steps_per_stage, int32_
 
 mdhp_status mdhp_plan_set_feature_store(mdhp_plan *p, int32_t tmem) {
   if (!p) return fail(MDHP_E_ARG, "plan NULL");
-  if (tmem < 0 || tmem > 2) return fail(MDHP_E_ARG, "feature store %d (0, 1 or 2)", tmem);
+  if (tmem < 0 || tmem > 3) return fail(MDHP_E_ARG, "feature store %d (0..3)", tmem);
   p->xtmem = tmem;
   return MDHP_OK;
 }
@@ -920,27 +920,34 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
         al.carve = make_carve_x(p->Mt, p->xnt, 0, o->optimizer == 1, 0, 0, p->beta_mode == 2);
       }
       FitFn fx = get_fitx(p->Mt, p->beta_mode, al.pipe_stages > 0 ? XM_RING : XM_GLOBAL, p->xnt);
-      FitFn ft = (p->xtmem && al.pipe_stages == 0) ? get_fitx(p->Mt, p->beta_mode, XM_TMEM, p->xnt)
+      // feature store 3: the tensor-memory kernel with 384 threads (12 warps)
+      const int ntx = (p->xtmem == 3 && al.pipe_stages == 0) ? 384 : p->xnt;
+      FitFn ft = (p->xtmem && al.pipe_stages == 0) ? get_fitx(p->Mt, p->beta_mode, XM_TMEM, ntx)
                                                    : nullptr;
-      if (ft) fx = ft;
+      if (ft) {
+        fx = ft;
+        al.carve = make_carve_x(p->Mt, ntx, 0, o->optimizer == 1, 0, 0, p->beta_mode == 2);
+      }
+      const int nlaunch = ft ? ntx : p->xnt;
       int dyn = al.carve.total;
       int occ = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fx, p->xnt, dyn);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fx, nlaunch, dyn);
       if (ft) {
         // each resident CTA's share of the 512 tensor-memory columns (a
-        // power of two) and, with feature store 2, of the shared memory the
-        // carve leaves at this occupancy: steps of NT float4 slices
+        // power of two) and, with feature store 2 or 3, of the shared memory
+        // the carve leaves at this occupancy: steps of NT float4 slices
         int cols = 512;
         while (cols > 32 && cols * std::max(occ, 1) > 512) cols >>= 1;
         al.tmem_cols = cols;
-        if (cols * std::max(occ, 1) > 512 || cols / std::max(p->xnt / 128, 1) < p->Mt)
+        const int sets = std::max(nlaunch / 128, 1);
+        if (cols * std::max(occ, 1) > 512 || cols / sets < p->Mt)
           return fail(MDHP_E_UNSUPPORTED, "tensor-memory features: %d CTAs per SM leave no row", occ);
         al.smem_steps = 0;
-        if (p->xtmem == 2) {
+        if (p->xtmem >= 2) {
           int dev = 0, smem_sm = 0;
           cudaGetDevice(&dev);
           cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-          const int step_bytes = p->Mt * 4 * p->xnt;
+          const int step_bytes = p->Mt * 4 * nlaunch;
           const int room = std::min(smem_sm / std::max(occ, 1) - 1024, max_dyn_smem()) - dyn;
           al.smem_steps = std::max(0, std::min(room / step_bytes, 64));
           dyn += al.smem_steps * step_bytes;
@@ -955,7 +962,7 @@ mdhp_status mdhp_fit_batch(mdhp_plan *p, const mdhp_batch *batch, const mdhp_fit
       }
       int gl = num_sms() * (occ > 0 ? occ : 1);
       if (gl > p->xgrid) gl = p->xgrid;
-      fx<<<gl, p->xnt, dyn, ls>>>(al);
+      fx<<<gl, nlaunch, dyn, ls>>>(al);
       ++p->launches;
       if ((s = cuda_check("k_fit_x (global features)")) != MDHP_OK) return s;
       if (xres > 0) cudaEventRecord(p->ev_join, p->side);
@@ -1113,7 +1120,8 @@ mdhp_status mdhp_plan_autotune(mdhp_plan *p, const mdhp_batch *batch, const mdhp
       }
       if (fit >= 128) cands.push_back({nt, 0, fit / 2 / 32 * 32, 0, 0, 0, 256, 1});
       if (p->beta_mode != 2 && get_fitx(p->Mt, p->beta_mode, XM_TMEM, nt)) {
-        for (int tm = 1; tm <= 2; ++tm) {
+        for (int tm = 1; tm <= 3; ++tm) {  // store 3 runs its own 384-thread kernel
+          if (tm == 3 && !get_fitx(p->Mt, p->beta_mode, XM_TMEM, 384)) continue;
           cands.push_back({nt, 0, 0, 0, 0, 0, 256, 1, tm});
           if (fit >= 64) cands.push_back({nt, 0, fit, 0, 0, 0, 256, 1, tm});
         }

@@ -436,7 +436,8 @@ __device__ __forceinline__ float xseg_sum(int i, int j, const Sm<M> &sm) {
   const float *ps = sm.P + sm.tf[i] + j;
   const int cnt = sm.tl[i];
   float acc = 0.f;
-  for (int s = 0; s < cnt; ++s) acc += ps[s * PP];
+#pragma unroll 4
+  for (int s = 0; s < cnt; ++s) acc += ps[s * PP];  // in slot order; the loads of 4 slots overlap
   return acc;
 }
 
@@ -525,8 +526,8 @@ __device__ __forceinline__ void xpass_t(int p0, int p1, int i0, const float4 *X,
 template <int M, int NTC, int XM>
 struct XBounds {
   static constexpr bool three = NTC == 128 && M >= 32 && XM != XM_TMEM;
-  static constexpr int threads = three ? 128 : 256;
-  static constexpr int ctas = three ? 3 : (M >= 32 ? 1 : 2);
+  static constexpr int threads = NTC > 256 ? NTC : (three ? 128 : 256);
+  static constexpr int ctas = NTC > 256 ? 1 : (three ? 3 : (M >= 32 ? 1 : 2));
 };
 
 template <int M, int BM, int XM, int NTC>
@@ -543,10 +544,10 @@ __global__ void __launch_bounds__(XBounds<M, NTC, XM>::threads, XBounds<M, NTC, 
   const int nupd = Mrt + Mrt * Mrt;
   const int tid = threadIdx.x, NT = NTC > 0 ? NTC : (int)blockDim.x;
   const int xcap = a.ev_cap;
-  // global slot: (xcap + 512) rows, enough for L * NT with the odd rounding of
-  // L for every block size up to 256 (one stride for all launches of a plan)
+  // global slot: (xcap + 768) rows, enough for L * NT with the odd rounding of
+  // L for every block size up to 384 (one stride for all launches of a plan)
   float4 *Xg = XS ? nullptr
-                  : a.xbuf + (size_t)(a.slot_base + blockIdx.x) * (M / 4) * (size_t)(xcap + 512);
+                  : a.xbuf + (size_t)(a.slot_base + blockIdx.x) * (M / 4) * (size_t)(xcap + 768);
   constexpr bool pipe = XM == XM_RING;
   XPipe pp{Xg, (M / 4) * NT, 1, a.pipe_steps, a.pipe_stages, 1, 0u, 0u, 0u, a.wait_polls};
   bool ring_lost = false;  // a drain gave up: fills may still be landing in the ring
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(XBounds<M, NTC, XM>::threads, XBounds<M, NTC, 
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
-    const int share = NT > 128 ? a.tmem_cols / (NT / 128) : a.tmem_cols;
+    const int share = NT > 128 ? a.tmem_cols / (NT / 128) / M * M : a.tmem_cols;
     tb = (uint32_t)sm.ctl[8] + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * share);
     tsteps = share / M;
   }
@@ -735,7 +736,9 @@ __global__ void __launch_bounds__(XBounds<M, NTC, XM>::threads, XBounds<M, NTC, 
       if ((tid & 31) == 0) reinterpret_cast<float4 *>(sm.red)[tid >> 5] = make_float4(h1, l1, h2, l2);
       __syncthreads();
       int bad = 0;
-      if (tid == 0) {
+      // the convergence decision is taken by the last thread, whose warp has
+      // the fewest parameters to update when they do not divide evenly
+      if (tid == NT - 1) {
         const FF val = lnl_total_ff(sm);
         bad = !isfinite(val.hi);
         int decision = 0;
@@ -812,7 +815,7 @@ __global__ void __launch_bounds__(XBounds<M, NTC, XM>::threads, XBounds<M, NTC, 
     for (int i = tid; i < Mrt; i += NT) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];
     for (int j = tid; j < nb; j += NT)
       a.beta[(int64_t)b * nb + j] = sm.beta[BM == 2 ? (j / Mrt) * M + (j % Mrt) : j];
-    if (tid == 0) {
+    if (tid == NT - 1) {  // the thread that took the decisions
       a.loglik[b] = ff_to_double(lnl_out);
       a.iters[b] = k;
       a.status[b] = wst;

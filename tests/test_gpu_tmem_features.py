@@ -65,7 +65,7 @@ def _close_params(a, b, rtol):
 
 
 @pytest.mark.parametrize("M,mode,nt,store", [(32, 0, 256, 1), (32, 0, 256, 2), (32, 1, 256, 2),
-                                              (24, 1, 256, 1)])
+                                              (24, 1, 256, 1), (32, 0, 256, 3), (24, 1, 256, 3)])
 def test_tmem_features_match_scratch_and_oracle(mdhp, wl, orc, M, mode, nt, store):
     iters = 30
     bt = _batch(wl, M, mode, 160, 4100 + M + 7 * mode + nt, 100, 6000)
@@ -75,24 +75,36 @@ def test_tmem_features_match_scratch_and_oracle(mdhp, wl, orc, M, mode, nt, stor
     assert np.all(st_t == 0) and np.all(st_g == 0)
     assert np.all(it_t == iters) and np.all(it_g == iters)
     assert np.all(np.abs(ll_t - ll_g) <= LL_RTOL * np.abs(ll_g))
-    for b in range(bt.B):
-        assert _close_params(mu_t[b], mu_g[b], P_RTOL), b
-        assert _close_params(al_t[b], al_g[b], P_RTOL), b
-    # the FP64 oracle on the longest, the shortest and random windows
+    if store < 3:
+        # the same threads own the same features: only the log sums' pairing
+        # differs, so the trajectories agree to the parameter tolerance
+        for b in range(bt.B):
+            assert _close_params(mu_t[b], mu_g[b], P_RTOL), b
+            assert _close_params(al_t[b], al_g[b], P_RTOL), b
+    # the FP64 oracle from the same cold start: lnL of every window; the
+    # parameters of the longest, the shortest and random windows (after a
+    # fixed count of Adam steps, the normalised step carries rounding in
+    # near-zero gradients into those parameters; store 3 runs 384 threads per
+    # window, another summation order, so the oracle is its reference)
+    B = bt.B
+    nb = 1 if mode == 0 else M
+    beta0 = np.asarray(bt.beta, dtype=np.float64).reshape(B, nb)
+    mu0 = np.zeros((B, M))
+    a0 = np.zeros((B, M, M))
+    for b in range(B):
+        _, ids, T, _ = bt.window(b)
+        mu0[b], a0[b] = orc.cold_init(ids.astype(np.int32), float(T), M, beta0[b], mode=mode)
+    o = orc.fit_opts(optimizer=1, max_iters=iters, lr=2e-2)
+    r = orc.fit_batch(bt.offsets, bt.t, bt.id, bt.T, M, mode, mu0, a0, beta0, o)
+    assert np.all(r["status"] == 0) and np.all(r["iters"] == iters)
+    assert np.all(np.abs(ll_t - r["lnL"]) <= LL_RTOL * np.abs(r["lnL"]))
     order = np.argsort(bt.counts, kind="stable")
     rng = np.random.default_rng(M + nt)
-    sample = sorted(set(int(b) for b in list(order[-2:]) + list(order[:2]) + list(rng.choice(bt.B, 3, replace=False))))
-    o = orc.fit_opts(optimizer=1, max_iters=iters, lr=2e-2)
+    sample = sorted(set(int(b) for b in list(order[-2:]) + list(order[:2]) + list(rng.choice(B, 3, replace=False))))
     for b in sample:
-        t, ids, T, _ = bt.window(b)
-        beta_b = np.asarray(bt.beta[b], dtype=np.float64)
-        m0, a0 = orc.cold_init(ids, float(T), M, beta_b, mode=mode)
-        r = orc.fit(t, ids, float(T), m0, a0, beta_b, o, mode=mode)
-        assert r["iters"] == iters
-        assert abs(ll_t[b] - r["lnL"]) <= LL_RTOL * abs(r["lnL"]), (b, ll_t[b], r["lnL"])
-        rm = r["mu"]
+        rm = r["mu"][b]
         assert np.all(np.abs(mu_t[b] - rm) <= P_RTOL * np.maximum(np.abs(rm), 1e-3 * np.abs(rm).max())), b
-        assert _close_params(al_t[b], r["alpha"], P_RTOL), b
+        assert _close_params(al_t[b], r["alpha"][b], P_RTOL), b
 
 
 def test_tmem_features_fit_to_tolerance(mdhp, wl):
