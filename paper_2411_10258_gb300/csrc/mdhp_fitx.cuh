@@ -62,14 +62,31 @@ __device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, in
   __syncthreads();
   const int c = tid;
   const int b0 = sm.bnd[c], b1 = sm.bnd[c + 1];
+#pragma unroll 4
   for (int n = b0; n < b1; ++n) ctr[ev.id(n) * NC + c] += 1;
   __syncthreads();
-  if (tid < M) {  // exclusive scan over chunks, per type, from the type's start
-    int run = sm.tstart[tid];
-    for (int cc = 0; cc < NC; ++cc) {
-      const int v = ctr[tid * NC + cc];
-      ctr[tid * NC + cc] = run;
-      run += v;
+  {  // exclusive scan over chunks, per type, from the type's start: one warp
+     // per type, each lane a run of G chunks (G odd: the lanes' reads and
+     // writes fall in distinct banks), the runs' totals scanned by shuffles
+    const int lane = tid & 31, nw = NT >> 5;
+    const int G = ((NC + 31) >> 5) | 1;
+    const int c0 = min(lane * G, NC), c1 = min(c0 + G, NC);
+    for (int i = tid >> 5; i < M; i += nw) {
+      int *row = ctr + i * NC;
+      int sum = 0;
+      for (int cc = c0; cc < c1; ++cc) sum += row[cc];
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int run = sm.tstart[i] + incl - sum;
+      for (int cc = c0; cc < c1; ++cc) {
+        const int v = row[cc];
+        row[cc] = run;
+        run += v;
+      }
     }
   }
   __syncthreads();
@@ -80,10 +97,13 @@ __device__ void build_features(int N, const EV &ev, int Mrt, Sm<M> &sm, XP X, in
   for (int j = 0; j < M; ++j) wk.R[j] = sm.encR[c * M + j];
   float tprev = sm.anc[c];
   int gs = b0;
+  float tnx = 0.f;  // the next event, loaded one step ahead
+  int unx = 0;
+  if (b0 < b1) ev.get(b0, tnx, unx);
   for (int n = b0; n < b1; ++n) {
-    float tn;
-    int un;
-    ev.get(n, tn, un);
+    const float tn = tnx;
+    const int un = unx;
+    if (n + 1 < b1) ev.get(n + 1, tnx, unx);
     if (tn > tprev) {
       for (int k = gs; k < n; ++k) wk.add(ev.id(k), ev.wt(k));
       wk.decay(tn - tprev);
@@ -736,10 +756,13 @@ __global__ void __launch_bounds__(XBounds<M, NTC, XM>::threads, XBounds<M, NTC, 
       if ((tid & 31) == 0) reinterpret_cast<float4 *>(sm.red)[tid >> 5] = make_float4(h1, l1, h2, l2);
       __syncthreads();
       int bad = 0;
-      // the convergence decision is taken by the last thread, whose warp has
-      // the fewest parameters to update when they do not divide evenly
-      if (tid == NT - 1) {
-        const FF val = lnl_total_ff(sm);
+      // the convergence decision is taken by lane 0 of the last warp (that
+      // warp has the fewest parameters to update when they do not divide
+      // evenly), after the warp has added the warps' partial sums as a tree
+      const int dec = NT - 32;
+      FF val{0.f, 0.f};
+      if (tid >= dec) val = lnl_total_ff_warp(sm.red, NT >> 5);
+      if (tid == dec) {
         bad = !isfinite(val.hi);
         int decision = 0;
         if (!bad) {
@@ -815,7 +838,7 @@ __global__ void __launch_bounds__(XBounds<M, NTC, XM>::threads, XBounds<M, NTC, 
     for (int i = tid; i < Mrt; i += NT) a.mu[(int64_t)b * Mrt + i] = sm.mu[i];
     for (int j = tid; j < nb; j += NT)
       a.beta[(int64_t)b * nb + j] = sm.beta[BM == 2 ? (j / Mrt) * M + (j % Mrt) : j];
-    if (tid == NT - 1) {  // the thread that took the decisions
+    if (tid == NT - 32) {  // the thread that took the decisions
       a.loglik[b] = ff_to_double(lnl_out);
       a.iters[b] = k;
       a.status[b] = wst;

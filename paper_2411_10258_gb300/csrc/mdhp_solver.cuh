@@ -613,8 +613,10 @@ __device__ __forceinline__ void pass1_chunk(int c, int s, int b0, int b1, float 
     wk.zero();
     float tprev = a0;
     int gs = b0;
+    float tnx = b0 < b1 ? ev.time(b0) : 0.f;  // the next time, loaded one step ahead
     for (int n = b0; n < b1; ++n) {
-      const float tn = ev.time(n);
+      const float tn = tnx;
+      if (n + 1 < b1) tnx = ev.time(n + 1);
       if (tn > tprev) {
         for (int k = gs; k < n; ++k) wk.add(slot_of<SPL>(s, ev.id(k)), ev.wt(k));
         wk.decay(tn - tprev);
@@ -859,6 +861,7 @@ __device__ int stage_and_validate(const float *tg, const int16_t *ug, const floa
   __syncthreads();
   int code = 0x7fffffff;
   if (tid == 0 && (!(T >= 0.f) || !isfinite(T))) code = kE_TIME_RANGE;
+#pragma unroll 4
   for (int n = tid; n < N; n += nt) {
     const float tv = tg[n];
     const int uv = (int)ug[n];
@@ -1133,6 +1136,26 @@ __device__ __forceinline__ FF lnl_total_ff(const Sm<M> &sm) {
     const float4 v = r4[w];
     p1 = ff_add(p1, FF{v.x, v.y});
     p23 = ff_add(p23, FF{v.z, v.w});
+  }
+  return ff_add(ff_mul(p1, kLn2Hi, kLn2Lo), p23);
+}
+
+// The same total formed by one warp: lane l < nw takes warp l's partials and
+// four shuffle rounds add them as a tree; lane 0 holds the total (nw <= 16).
+__device__ __forceinline__ FF lnl_total_ff_warp(const double *red, int nw) {
+  const int lane = threadIdx.x & 31;
+  FF p1{0.f, 0.f}, p23{0.f, 0.f};
+  if (lane < nw) {
+    const float4 v = reinterpret_cast<const float4 *>(red)[lane];
+    p1 = FF{v.x, v.y};
+    p23 = FF{v.z, v.w};
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const FF q1{__shfl_down_sync(0xffffffffu, p1.hi, o), __shfl_down_sync(0xffffffffu, p1.lo, o)};
+    const FF q23{__shfl_down_sync(0xffffffffu, p23.hi, o), __shfl_down_sync(0xffffffffu, p23.lo, o)};
+    p1 = ff_add(p1, q1);
+    p23 = ff_add(p23, q23);
   }
   return ff_add(ff_mul(p1, kLn2Hi, kLn2Lo), p23);
 }
