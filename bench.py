@@ -184,7 +184,7 @@ class ClockSampler:
 # (--feature-store S); keyed by (T, S).
 # Summary: profiles/k_fit_x_M32_dram_headline_fit.md.
 HEADLINE_FIT_DRAM = {(128, 0): 1.81e12 + 24.81e9, (256, 0): 926.65e9 + 12.74e9,
-                     (256, 2): 189.462e9 + 11.065e9, (256, 3): 326.645e9 + 12.090e9}
+                     (256, 2): 189.462e9 + 11.065e9, (256, 3): 335.468e9 + 12.052e9}
 
 
 def measured_peaks():
@@ -1041,7 +1041,7 @@ def run_headline(args):
                                      "and the loads of the feature steps past those kept in "
                                      "tensor and shared memory; DRAM (0.2-0.34 TB per fit) and "
                                      "the FMA pipe do not bind "
-                                     "(profiles/k_fit_x_M32_tmem_full_set_8192windows.md)")
+                                     "(profiles/k_fit_x_M32_store3_full_set_8192windows.md)")
                                     if cold_shape.get("feature_store", 0) else
                                     ("latency of the streamed feature loads and the per-event FMA "
                                      "chains: neither DRAM bandwidth (0.9-1.8 TB per fit) nor the "
