@@ -4,17 +4,20 @@ memory (mdhp_plan_set_feature_store).
 The features x_n = R(t_n) of a fixed-beta window (Sec. IV-B.3 Stage 1,
 "Decoupling") are computed once per fit; with the feature store on, the
 first steps of each thread's range live in the SM's tensor memory (and,
-with store 2, the next ones in shared memory) and only the rest is re-read
-from the plan's scratch at every iteration.  Windows
-shorter than the tensor-memory rows, windows that span both tiers, ragged
-tails, a width below the template's (M = 24 in the 32-wide kernel), scalar
-and per-source beta and both stores are fitted and compared
+with stores 2 and 3, the next ones in shared memory; store 3 runs 384
+threads per window) and only the rest is re-read from the plan's scratch at
+every iteration.  Windows shorter than the tensor-memory rows, windows that
+span every tier, ragged tails, a width below the template's (M = 24 in the
+32-wide kernel), scalar and per-source beta and stores 1-3 are fitted and
+compared
 
 * with the same plan with the feature store off (same statuses and
-  iteration counts; lnL within 1e-5 relative, parameters within 1e-4 of the
-  group's scale: only the order of the per-thread log sums differs), and
-* with the FP64 oracle re-fitting sampled windows from the same cold start
-  (lnL 1e-5 relative, parameters 1e-4 of the group's scale)."""
+  iteration counts, lnL within 1e-5 relative; for stores 1 and 2, whose
+  threads own the same features, parameters within 1e-4 of the group's
+  scale), and
+* with the FP64 oracle re-fitting every window from the same cold start
+  (lnL 1e-5 relative) and, for the longest, the shortest and random
+  windows, the parameters (1e-4 of the group's scale)."""
 import numpy as np
 import pytest
 
