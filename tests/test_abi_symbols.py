@@ -51,3 +51,20 @@ def test_missing_library_fails_loudly(tmp_path):
 
     with pytest.raises(RuntimeError):
         _lib.load(str(tmp_path / "nope.so"))
+
+
+def test_plan_setters_reject_bad_arguments_without_a_gpu():
+    """The plan's tuning setters check their arguments on the host before any
+    CUDA call: a NULL plan and out-of-range values return MDHP_E_ARG with a
+    message, and the getters report -1 for a NULL plan."""
+    from paper_2411_10258_gb300 import build, _lib
+
+    lib = _lib.load(build.build())
+    null = ctypes.c_void_p(None)
+    assert lib.mdhp_plan_set_feature_store(null, 1) == _lib.E_ARG
+    assert b"NULL" in lib.mdhp_last_error()
+    assert lib.mdhp_plan_get_feature_store(null) == -1
+    assert lib.mdhp_plan_set_pipeline(null, 2, 2) == _lib.E_ARG
+    assert lib.mdhp_plan_set_split(null, 1, 256, 1) == _lib.E_ARG
+    assert lib.mdhp_plan_set_wait_limit(null, 0) == _lib.E_ARG
+    assert lib.mdhp_plan_last_launches(null) == -1
