@@ -9,8 +9,6 @@ columns, the global scratch slot of (xcap + 768) rows in step-major order).
 It checks that every access stays inside what was allocated and that no
 two threads touch the same tensor-memory cell, for every block size the
 kernel is built for and every occupancy the host could see."""
-import itertools
-
 import pytest
 
 M = 32  # the template width the tensor-memory kernels are built for
