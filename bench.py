@@ -1306,8 +1306,7 @@ def run_gemm(args):
     peaks, src = measured_peaks()
     flops = 2.0 * M * N * K
     res = {}
-    sampler = ClockSampler(0, os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None,
-                           name="gemm")
+    sampler = ClockSampler(0, args.clocks_dir, name="gemm")
     with sampler:
         for name, engine in (("tcgen05", 0), ("tcgen05_copies", 2), ("mma_sync", 1)):
             for _ in range(max(args.warmup, 3)):
